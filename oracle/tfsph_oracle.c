@@ -1,0 +1,719 @@
+/*
+ * FP64 CPU oracle of one two-fluid SPH (TFSPH) time step with the implicit
+ * "drag in cell" (SPH-IDIC) interphase drag of Stoyanovskaya et al.,
+ * "Monodisperse gas-solid mixtures with intense interphase interaction in
+ * two-fluid SPH" (arXiv:1908.01682).
+ *
+ * TEST INFRASTRUCTURE ONLY. This file is the independent checker of the GPU
+ * library: only the test suite, the smoke check and the CPU-baseline leg of
+ * the benchmark load it. It shares no code, header, table or constant with
+ * the CUDA path, and the product path never calls it.
+ *
+ * Everything is a plain loop in double precision, following the method in the
+ * paper's order:
+ *   - two-fluid momentum equations in K form (Sec. 2, Eq. 7), gas pressure
+ *     acceleration as the symmetric SPH sum of the first term of Eq. 19;
+ *   - decomposition of the domain into disjoint Euler cells holding N gas and
+ *     L dust particles (Sec. 2.3), eps* = m_d L / (m_g N) (Eq. 17),
+ *     K* = rho*_d / t*_stop and rho*_g = rho*_d / eps* (Eq. 18);
+ *   - gas and dust velocity equations with drag taken implicitly against the
+ *     cell-mean velocity of the other phase (Eqs. 19-20), cell means v_*, u_*
+ *     (Eq. 21), first-order time discretisation (the "parsimonious" solve the
+ *     paper states but does not print; see orc_step).
+ *
+ * Readings of points the paper leaves open (each one is listed in the design
+ * notes of the repository):
+ *   - summation density with the self term, fixed h; M4 cubic spline kernel
+ *     with support 2h (the paper names no kernel);
+ *   - isothermal p = cs^2 rho, or adiabatic p = (gamma-1) rho e with the
+ *     standard SPH energy equation and Monaghan artificial viscosity;
+ *   - t*_stop = arithmetic mean of the per-particle stopping times of the
+ *     cell's dust (harmonic mean selectable); rho*_d cancels out;
+ *   - cells with N = 0 or L = 0 get no drag this step;
+ *   - positions advance with the new velocities, x' = x + tau v';
+ *   - particles are ordered by (cell key, particle id).
+ *
+ * Cell keys and neighbour membership are integer decisions taken from
+ * floating point. They are made in the precision of the path under test
+ * (binary32 when decide_fp32 = 1, binary64 otherwise), so both sides take
+ * the same decision; every value is then computed in binary64.
+ *
+ * Build with -ffp-contract=off so that the binary32 decisions are plain
+ * IEEE operations (no fused multiply-add).
+ */
+#include <math.h>
+#include <stdint.h>
+#include <stdlib.h>
+#include <string.h>
+
+#define ORC_OK 0
+#define ORC_E_ARG 1
+#define ORC_E_OOM 2
+
+typedef struct {
+    int32_t dim;          /* 1, 2 or 3 */
+    int32_t decide_fp32;  /* 1: keys and neighbour membership in binary32 */
+    int32_t eos;          /* 0 isothermal, 1 adiabatic */
+    int32_t tstar_mode;   /* 0 arithmetic mean of t_j, 1 harmonic mean */
+    int32_t periodic[3];
+    int32_t brute;        /* 1: all-pairs neighbour search, 0: cell lists */
+    double lo[3], hi[3];
+    double h, cell_size;
+    double m_gas, m_dust;
+    double cs, gamma;
+    double av_alpha, av_beta;
+} orc_params;
+
+/* ------------------------------------------------------------------------ */
+/* Smoothing kernel: M4 cubic spline, support 2h.                            */
+/* W(r,h) = sigma_d / h^d * { 1 - 3/2 q^2 + 3/4 q^3   (0 <= q < 1)           */
+/*                            1/4 (2 - q)^3           (1 <= q < 2)           */
+/*                            0                       (q >= 2) }, q = r/h    */
+/* sigma_1 = 2/3, sigma_2 = 10/(7 pi), sigma_3 = 1/pi (unit integral).      */
+/* ------------------------------------------------------------------------ */
+static double orc_sigma(int dim)
+{
+    if (dim == 1) return 2.0 / 3.0;
+    if (dim == 2) return 10.0 / (7.0 * M_PI);
+    return 1.0 / M_PI;
+}
+
+double orc_W(int dim, double h, double r)
+{
+    double q = r / h;
+    double norm = orc_sigma(dim) / pow(h, dim);
+    if (q < 1.0) return norm * (1.0 - 1.5 * q * q + 0.75 * q * q * q);
+    if (q < 2.0) return norm * 0.25 * (2.0 - q) * (2.0 - q) * (2.0 - q);
+    return 0.0;
+}
+
+/* dW/dr */
+double orc_dWdr(int dim, double h, double r)
+{
+    double q = r / h;
+    double norm = orc_sigma(dim) / pow(h, dim + 1);
+    if (q < 1.0) return norm * (-3.0 * q + 2.25 * q * q);
+    if (q < 2.0) return norm * (-0.75 * (2.0 - q) * (2.0 - q));
+    return 0.0;
+}
+
+/* ------------------------------------------------------------------------ */
+/* Euler cells: uniform axis-aligned grid from lo, n_d = floor(L_d / size).  */
+/* ------------------------------------------------------------------------ */
+int orc_ncell(const orc_params *P, int32_t ncell[3])
+{
+    for (int d = 0; d < 3; ++d) {
+        if (d >= P->dim) { ncell[d] = 1; continue; }
+        double L = P->hi[d] - P->lo[d];
+        double n = floor(L / P->cell_size);
+        if (n < 1.0) n = 1.0;
+        ncell[d] = (int32_t)n;
+    }
+    return ORC_OK;
+}
+
+/* Cell coordinate of one position along axis d, clamped to [0, n-1]. */
+static int64_t orc_axis_cell(const orc_params *P, int d, int32_t n, double x)
+{
+    double t;
+    if (P->decide_fp32) {
+        float inv = (float)((double)n / (P->hi[d] - P->lo[d]));
+        float xf = (float)x;
+        float lof = (float)P->lo[d];
+        float tf = (xf - lof) * inv;
+        t = floor((double)tf);
+    } else {
+        double inv = (double)n / (P->hi[d] - P->lo[d]);
+        t = floor((x - P->lo[d]) * inv);
+    }
+    if (t < 0.0) t = 0.0;
+    if (t > (double)(n - 1)) t = (double)(n - 1);
+    return (int64_t)t;
+}
+
+/* key = ix + nx (iy + ny iz); x is the position of one particle, x[d]. */
+static int64_t orc_key(const orc_params *P, const int32_t nc[3], const double x[3])
+{
+    int64_t c[3] = {0, 0, 0};
+    for (int d = 0; d < P->dim; ++d) c[d] = orc_axis_cell(P, d, nc[d], x[d]);
+    return c[0] + (int64_t)nc[0] * (c[1] + (int64_t)nc[1] * c[2]);
+}
+
+/* ------------------------------------------------------------------------ */
+/* Pair geometry. Membership r^2 < (2h)^2 decided in the path's precision.   */
+/* d[] receives x_a - x_b (minimum image on periodic axes) in binary64.      */
+/* ------------------------------------------------------------------------ */
+static int orc_pair(const orc_params *P, const double xa[3], const double xb[3],
+                    double d[3], double *r2)
+{
+    int inside;
+    if (P->decide_fp32) {
+        float acc = 0.0f;
+        for (int k = 0; k < P->dim; ++k) {
+            float dx = (float)xa[k] - (float)xb[k];
+            if (P->periodic[k]) {
+                float L = (float)(P->hi[k] - P->lo[k]);
+                float half = (float)(0.5 * (P->hi[k] - P->lo[k]));
+                if (dx > half) dx = dx - L;
+                else if (dx < -half) dx = dx + L;
+            }
+            float sq = dx * dx;
+            acc = (k == 0) ? sq : acc + sq;
+        }
+        float lim = (float)(4.0 * P->h * P->h);
+        inside = acc < lim;
+    } else {
+        double acc = 0.0;
+        for (int k = 0; k < P->dim; ++k) {
+            double dx = xa[k] - xb[k];
+            if (P->periodic[k]) {
+                double L = P->hi[k] - P->lo[k];
+                double half = 0.5 * (P->hi[k] - P->lo[k]);
+                if (dx > half) dx = dx - L;
+                else if (dx < -half) dx = dx + L;
+            }
+            double sq = dx * dx;
+            acc = (k == 0) ? sq : acc + sq;
+        }
+        inside = acc < 4.0 * P->h * P->h;
+    }
+    double s = 0.0;
+    for (int k = 0; k < 3; ++k) {
+        d[k] = 0.0;
+        if (k >= P->dim) continue;
+        double dx = xa[k] - xb[k];
+        if (P->periodic[k]) {
+            double L = P->hi[k] - P->lo[k];
+            if (dx > 0.5 * L) dx -= L;
+            else if (dx < -0.5 * L) dx += L;
+        }
+        d[k] = dx;
+        s += dx * dx;
+    }
+    *r2 = s;
+    return inside;
+}
+
+/* ------------------------------------------------------------------------ */
+/* Sorting into cells: ascending (key, id).                                  */
+/* ------------------------------------------------------------------------ */
+typedef struct { int64_t key; int64_t id; } orc_kv;
+
+static int orc_kv_cmp(const void *a, const void *b)
+{
+    const orc_kv *x = (const orc_kv *)a, *y = (const orc_kv *)b;
+    if (x->key != y->key) return x->key < y->key ? -1 : 1;
+    if (x->id != y->id) return x->id < y->id ? -1 : 1;
+    return 0;
+}
+
+static void orc_get_pos(int dim, int64_t n, const double *x, int64_t i, double p[3])
+{
+    p[0] = p[1] = p[2] = 0.0;
+    for (int d = 0; d < dim; ++d) p[d] = x[(int64_t)d * n + i];
+}
+
+/* keys[i] per particle (id order); perm[s] = id at sorted slot s;
+ * cstart[c] = first slot of cell c, cstart[ncells] = n. */
+int orc_bin(const orc_params *P, int64_t n, const double *x,
+            int64_t *keys, int64_t *perm, int64_t *cstart)
+{
+    int32_t nc[3];
+    orc_ncell(P, nc);
+    int64_t ncells = (int64_t)nc[0] * nc[1] * nc[2];
+    orc_kv *kv = (orc_kv *)malloc(sizeof(orc_kv) * (size_t)(n > 0 ? n : 1));
+    if (!kv) return ORC_E_OOM;
+    for (int64_t i = 0; i < n; ++i) {
+        double p[3];
+        orc_get_pos(P->dim, n, x, i, p);
+        kv[i].key = orc_key(P, nc, p);
+        kv[i].id = i;
+        if (keys) keys[i] = kv[i].key;
+    }
+    qsort(kv, (size_t)n, sizeof(orc_kv), orc_kv_cmp);
+    if (perm) for (int64_t s = 0; s < n; ++s) perm[s] = kv[s].id;
+    if (cstart) {
+        for (int64_t c = 0; c <= ncells; ++c) cstart[c] = 0;
+        for (int64_t s = 0; s < n; ++s) cstart[kv[s].key + 1] += 1;
+        for (int64_t c = 0; c < ncells; ++c) cstart[c + 1] += cstart[c];
+    }
+    free(kv);
+    return ORC_OK;
+}
+
+/* ------------------------------------------------------------------------ */
+/* Neighbour candidates. Brute force: every particle. Cell lists: every      */
+/* distinct cell within +-R of the particle's cell, R = floor(2h/w) + 2,     */
+/* which is wider than any pair within 2h can reach. The membership test     */
+/* decides; the candidate set only has to contain the neighbours.           */
+/* ------------------------------------------------------------------------ */
+typedef struct {
+    const orc_params *P;
+    int32_t nc[3];
+    int64_t n;
+    const double *x;
+    const int64_t *perm;    /* sorted slot -> id */
+    const int64_t *cstart;  /* cell -> first slot */
+} orc_grid;
+
+/* Distinct cell coordinates along axis d around cell c; returns count. */
+static int orc_axis_window(const orc_grid *G, int d, int64_t c, int64_t *out)
+{
+    int32_t n = G->nc[d];
+    if (d >= G->P->dim) { out[0] = 0; return 1; }
+    double w = (G->P->hi[d] - G->P->lo[d]) / (double)n;
+    int64_t R = (int64_t)floor(2.0 * G->P->h / w) + 2;
+    int cnt = 0;
+    if (G->P->periodic[d]) {
+        if (2 * R + 1 >= n) {
+            for (int64_t k = 0; k < n; ++k) out[cnt++] = k;
+        } else {
+            for (int64_t o = -R; o <= R; ++o) out[cnt++] = ((c + o) % n + n) % n;
+        }
+    } else {
+        for (int64_t o = -R; o <= R; ++o) {
+            int64_t k = c + o;
+            if (k >= 0 && k < n) out[cnt++] = k;
+        }
+    }
+    return cnt;
+}
+
+/* Calls visit(ctx, b) for every candidate b of particle position p. */
+typedef void (*orc_visit_fn)(void *ctx, int64_t b);
+
+static void orc_foreach_candidate(const orc_grid *G, const double p[3],
+                                  orc_visit_fn visit, void *ctx)
+{
+    if (G->P->brute) {
+        for (int64_t b = 0; b < G->n; ++b) visit(ctx, b);
+        return;
+    }
+    int64_t cc[3] = {0, 0, 0};
+    for (int d = 0; d < G->P->dim; ++d) cc[d] = orc_axis_cell(G->P, d, G->nc[d], p[d]);
+    int64_t *wx = (int64_t *)malloc(sizeof(int64_t) * (size_t)(G->nc[0] + 8));
+    int64_t *wy = (int64_t *)malloc(sizeof(int64_t) * (size_t)(G->nc[1] + 8));
+    int64_t *wz = (int64_t *)malloc(sizeof(int64_t) * (size_t)(G->nc[2] + 8));
+    int nx = orc_axis_window(G, 0, cc[0], wx);
+    int ny = orc_axis_window(G, 1, cc[1], wy);
+    int nz = orc_axis_window(G, 2, cc[2], wz);
+    for (int iz = 0; iz < nz; ++iz)
+        for (int iy = 0; iy < ny; ++iy)
+            for (int ix = 0; ix < nx; ++ix) {
+                int64_t key = wx[ix] + (int64_t)G->nc[0] * (wy[iy] + (int64_t)G->nc[1] * wz[iz]);
+                for (int64_t s = G->cstart[key]; s < G->cstart[key + 1]; ++s) visit(ctx, G->perm[s]);
+            }
+    free(wx);
+    free(wy);
+    free(wz);
+}
+
+/* ------------------------------------------------------------------------ */
+/* Summation density rho_a = sum_b m W(|r_ab|, h), self term included.       */
+/* Also the neighbour count and an order-free fingerprint of the neighbour   */
+/* set: sum over neighbours of (id_b + 1) * 0x9E3779B97F4A7C15 mod 2^64.     */
+/* ------------------------------------------------------------------------ */
+typedef struct {
+    const orc_grid *G;
+    double pa[3];
+    double m;
+    double rho;
+    int64_t count;
+    uint64_t fprint;
+} orc_dens_ctx;
+
+static void orc_dens_visit(void *vctx, int64_t b)
+{
+    orc_dens_ctx *c = (orc_dens_ctx *)vctx;
+    double pb[3], d[3], r2;
+    orc_get_pos(c->G->P->dim, c->G->n, c->G->x, b, pb);
+    if (!orc_pair(c->G->P, c->pa, pb, d, &r2)) return;
+    c->rho += c->m * orc_W(c->G->P->dim, c->G->P->h, sqrt(r2));
+    c->count += 1;
+    c->fprint += (uint64_t)(b + 1) * 0x9E3779B97F4A7C15ull;
+}
+
+static int orc_make_grid(const orc_params *P, int64_t n, const double *x, orc_grid *G,
+                         int64_t **perm, int64_t **cstart)
+{
+    G->P = P;
+    orc_ncell(P, G->nc);
+    G->n = n;
+    G->x = x;
+    int64_t ncells = (int64_t)G->nc[0] * G->nc[1] * G->nc[2];
+    *perm = (int64_t *)malloc(sizeof(int64_t) * (size_t)(n > 0 ? n : 1));
+    *cstart = (int64_t *)malloc(sizeof(int64_t) * (size_t)(ncells + 1));
+    if (!*perm || !*cstart) return ORC_E_OOM;
+    orc_bin(P, n, x, NULL, *perm, *cstart);
+    G->perm = *perm;
+    G->cstart = *cstart;
+    return ORC_OK;
+}
+
+/* Density of one particle set (gas or dust) of particle mass m. */
+int orc_density(const orc_params *P, int64_t n, const double *x, double m,
+                double *rho, int64_t *count, uint64_t *fprint)
+{
+    orc_grid G;
+    int64_t *perm = NULL, *cstart = NULL;
+    if (orc_make_grid(P, n, x, &G, &perm, &cstart) != ORC_OK) { free(perm); free(cstart); return ORC_E_OOM; }
+#pragma omp parallel for schedule(dynamic, 256)
+    for (int64_t a = 0; a < n; ++a) {
+        orc_dens_ctx c;
+        c.G = &G;
+        orc_get_pos(P->dim, n, x, a, c.pa);
+        c.m = m;
+        c.rho = 0.0;
+        c.count = 0;
+        c.fprint = 0;
+        orc_foreach_candidate(&G, c.pa, orc_dens_visit, &c);
+        rho[a] = c.rho;
+        if (count) count[a] = c.count;
+        if (fprint) fprint[a] = c.fprint;
+    }
+    free(perm);
+    free(cstart);
+    return ORC_OK;
+}
+
+/* ------------------------------------------------------------------------ */
+/* Equation of state.                                                        */
+/* ------------------------------------------------------------------------ */
+static double orc_pressure(const orc_params *P, double rho, double e)
+{
+    if (P->eos == 1) return (P->gamma - 1.0) * rho * e;
+    return P->cs * P->cs * rho;
+}
+
+static double orc_sound(const orc_params *P, double e)
+{
+    if (P->eos == 1) return sqrt(P->gamma * (P->gamma - 1.0) * e);
+    return P->cs;
+}
+
+/* ------------------------------------------------------------------------ */
+/* Gas pressure acceleration (first term of Eq. 19) and, with artificial    */
+/* viscosity on, Monaghan's Pi_ab; energy rate of the adiabatic gas.         */
+/*   A_a   = - sum_b m (p_a/rho_a^2 + p_b/rho_b^2 + Pi_ab) grad_a W_ab       */
+/*   de_a  =   sum_b m (p_a/rho_a^2 + Pi_ab / 2) (v_a - v_b) . grad_a W_ab    */
+/*   grad_a W_ab = (r_a - r_b) / r * dW/dr                                   */
+/*   Pi_ab = (-alpha cbar mu + beta mu^2) / rhobar  if (v_ab . r_ab) < 0      */
+/*   mu = h (v_ab . r_ab) / (r^2 + 0.01 h^2)                                  */
+/* ------------------------------------------------------------------------ */
+typedef struct {
+    const orc_grid *G;
+    int64_t a;
+    double pa[3], va[3];
+    const double *v, *rho, *pr, *cs;
+    double acc[3];
+    double dedt;
+} orc_force_ctx;
+
+static void orc_force_visit(void *vctx, int64_t b)
+{
+    orc_force_ctx *c = (orc_force_ctx *)vctx;
+    const orc_params *P = c->G->P;
+    int64_t n = c->G->n;
+    double pb[3], d[3], r2;
+    if (b == c->a) return;
+    orc_get_pos(P->dim, n, c->G->x, b, pb);
+    if (!orc_pair(P, c->pa, pb, d, &r2)) return;
+    double r = sqrt(r2);
+    if (r <= 0.0) return; /* coincident particles exert no pressure force */
+    double dw = orc_dWdr(P->dim, P->h, r);
+    double grad[3];
+    for (int k = 0; k < 3; ++k) grad[k] = d[k] / r * dw;
+    double vab[3] = {0, 0, 0};
+    double vr = 0.0;
+    for (int k = 0; k < P->dim; ++k) {
+        vab[k] = c->va[k] - c->v[(int64_t)k * n + b];
+        vr += vab[k] * d[k];
+    }
+    double qa = c->pr[c->a] / (c->rho[c->a] * c->rho[c->a]);
+    double qb = c->pr[b] / (c->rho[b] * c->rho[b]);
+    double pi = 0.0;
+    if ((P->av_alpha > 0.0 || P->av_beta > 0.0) && vr < 0.0) {
+        double mu = P->h * vr / (r2 + 0.01 * P->h * P->h);
+        double cbar = 0.5 * (c->cs[c->a] + c->cs[b]);
+        double rbar = 0.5 * (c->rho[c->a] + c->rho[b]);
+        pi = (-P->av_alpha * cbar * mu + P->av_beta * mu * mu) / rbar;
+    }
+    double m = P->m_gas;
+    double vg = 0.0;
+    for (int k = 0; k < P->dim; ++k) {
+        c->acc[k] -= m * (qa + qb + pi) * grad[k];
+        vg += vab[k] * grad[k];
+    }
+    c->dedt += m * (qa + 0.5 * pi) * vg;
+}
+
+/* acc[dim*n], dedt[n] (nullable) for every gas particle. */
+int orc_accel(const orc_params *P, int64_t n, const double *x, const double *v,
+              const double *e, const double *rho, double *acc, double *dedt)
+{
+    orc_grid G;
+    int64_t *perm = NULL, *cstart = NULL;
+    double *pr = (double *)malloc(sizeof(double) * (size_t)(n > 0 ? n : 1));
+    double *cs = (double *)malloc(sizeof(double) * (size_t)(n > 0 ? n : 1));
+    if (!pr || !cs || orc_make_grid(P, n, x, &G, &perm, &cstart) != ORC_OK) {
+        free(pr); free(cs); free(perm); free(cstart);
+        return ORC_E_OOM;
+    }
+    for (int64_t a = 0; a < n; ++a) {
+        double ea = e ? e[a] : 0.0;
+        pr[a] = orc_pressure(P, rho[a], ea);
+        cs[a] = orc_sound(P, ea);
+    }
+#pragma omp parallel for schedule(dynamic, 256)
+    for (int64_t a = 0; a < n; ++a) {
+        orc_force_ctx c;
+        c.G = &G;
+        c.a = a;
+        orc_get_pos(P->dim, n, x, a, c.pa);
+        for (int k = 0; k < 3; ++k) c.va[k] = k < P->dim ? v[(int64_t)k * n + a] : 0.0;
+        c.v = v;
+        c.rho = rho;
+        c.pr = pr;
+        c.cs = cs;
+        c.acc[0] = c.acc[1] = c.acc[2] = 0.0;
+        c.dedt = 0.0;
+        orc_foreach_candidate(&G, c.pa, orc_force_visit, &c);
+        for (int k = 0; k < P->dim; ++k) acc[(int64_t)k * n + a] = c.acc[k];
+        if (dedt) dedt[a] = c.dedt;
+    }
+    free(pr);
+    free(cs);
+    free(perm);
+    free(cstart);
+    return ORC_OK;
+}
+
+/* ------------------------------------------------------------------------ */
+/* Courant time step (Eq. 4): tau = CFL h / max over moving gas of           */
+/* max(|v_a|, c_a).                                                           */
+/* ------------------------------------------------------------------------ */
+double orc_max_dt(const orc_params *P, int64_t n, const double *v, const double *e,
+                  const uint8_t *frozen, double cfl)
+{
+    double vmax = 0.0;
+    for (int64_t a = 0; a < n; ++a) {
+        if (frozen && frozen[a]) continue;
+        double s = 0.0;
+        for (int k = 0; k < P->dim; ++k) s += v[(int64_t)k * n + a] * v[(int64_t)k * n + a];
+        double sp = sqrt(s);
+        double c = orc_sound(P, e ? e[a] : 0.0);
+        double m = sp > c ? sp : c;
+        if (m > vmax) vmax = m;
+    }
+    return cfl * P->h / vmax;
+}
+
+/* ------------------------------------------------------------------------ */
+/* One SPH-IDIC step (Sec. 2.3, Eqs. 17-21), in place.                       */
+/*                                                                           */
+/* With K^/rho^_g = eps^/t^ and K^/rho^_d = 1/t^ (Eq. 18; ^ marks a cell    */
+/* value), the first-order                                                   */
+/* implicit scheme for a cell with N > 0 gas and L > 0 dust reads            */
+/*   (v_a' - v_a)/tau = A_a + g - (eps^/t^) (v_a' - u_^')      (Eq. 19)      */
+/*   (u_j' - u_j)/tau = g + (1/t^) (v_^' - u_j')               (Eq. 20)      */
+/* with v_^, u_^ the cell means (Eq. 21). Averaging the first over the       */
+/* cell's gas and the second over its dust gives two equations for the     */
+/* new means; their difference fixes the new slip w' = v_^' - u_^':         */
+/*   w' (1 + tau (1 + eps^)/t^) = w + tau Abar,    w = v_^ - u_^            */
+/*   u_^' = u_^ + tau g + (tau/t^) w',   v_^' = u_^' + w'                  */
+/* after which each particle equation is linear in its own new velocity.   */
+/* ------------------------------------------------------------------------ */
+/* Periodic image of x in [lo, hi), whatever the number of periods crossed. */
+static double orc_wrap(double x, double lo, double hi)
+{
+    double L = hi - lo;
+    double y = x - lo;
+    y -= L * floor(y / L);
+    double r = lo + y;
+    if (r >= hi) r = lo;
+    if (r < lo) r = lo;
+    return r;
+}
+
+typedef struct {
+    /* outputs, each nullable */
+    double *rho_g;          /* [ng] density used in the step */
+    double *acc_g;          /* [dim*ng] pressure (+viscous) acceleration */
+    double *dedt_g;         /* [ng] */
+    int64_t *nb_count;      /* [ng] */
+    uint64_t *nb_fprint;    /* [ng] */
+    int64_t *keys_g, *keys_d;     /* [ng], [nd] per particle (id order) */
+    int64_t *perm_g, *perm_d;     /* [ng], [nd] id at sorted slot */
+    int64_t *cstart_g, *cstart_d; /* [ncells+1] */
+    int64_t n_drag_cells;         /* cells with N > 0 and L > 0 */
+} orc_step_out;
+
+int orc_step(const orc_params *P, int64_t ng, int64_t nd,
+             double *gx, double *gv, double *ge, const uint8_t *gfrozen,
+             double *dx, double *du, const double *tstop,
+             double tau, const double g[3], const double *acc_override,
+             orc_step_out *out)
+{
+    int dim = P->dim;
+    int32_t nc[3];
+    orc_ncell(P, nc);
+    int64_t ncells = (int64_t)nc[0] * nc[1] * nc[2];
+    if (dim < 1 || dim > 3 || tau <= 0.0) return ORC_E_ARG;
+
+    /* 1. Cells and sorting. */
+    int64_t *kg = (int64_t *)malloc(sizeof(int64_t) * (size_t)(ng > 0 ? ng : 1));
+    int64_t *kd = (int64_t *)malloc(sizeof(int64_t) * (size_t)(nd > 0 ? nd : 1));
+    int64_t *pg = (int64_t *)malloc(sizeof(int64_t) * (size_t)(ng > 0 ? ng : 1));
+    int64_t *pd = (int64_t *)malloc(sizeof(int64_t) * (size_t)(nd > 0 ? nd : 1));
+    int64_t *sg = (int64_t *)malloc(sizeof(int64_t) * (size_t)(ncells + 1));
+    int64_t *sd = (int64_t *)malloc(sizeof(int64_t) * (size_t)(ncells + 1));
+    double *rho = (double *)malloc(sizeof(double) * (size_t)(ng > 0 ? ng : 1));
+    double *acc = (double *)calloc((size_t)(dim * (ng > 0 ? ng : 1)), sizeof(double));
+    double *dedt = (double *)calloc((size_t)(ng > 0 ? ng : 1), sizeof(double));
+    /* per-cell: N, L, sum v, sum u, sum A, sum t (or sum 1/t) */
+    double *cN = (double *)calloc((size_t)ncells, sizeof(double));
+    double *cL = (double *)calloc((size_t)ncells, sizeof(double));
+    double *cv = (double *)calloc((size_t)(3 * ncells), sizeof(double));
+    double *cu = (double *)calloc((size_t)(3 * ncells), sizeof(double));
+    double *cA = (double *)calloc((size_t)(3 * ncells), sizeof(double));
+    double *ct = (double *)calloc((size_t)ncells, sizeof(double));
+    int rc = ORC_OK;
+    if (!kg || !kd || !pg || !pd || !sg || !sd || !rho || !acc || !dedt || !cN || !cL || !cv ||
+        !cu || !cA || !ct) {
+        rc = ORC_E_OOM;
+        goto done;
+    }
+    orc_bin(P, ng, gx, kg, pg, sg);
+    orc_bin(P, nd, dx, kd, pd, sd);
+
+    /* 2. Gas summation density and pressure. */
+    if (ng > 0) orc_density(P, ng, gx, P->m_gas, rho, out ? out->nb_count : NULL,
+                            out ? out->nb_fprint : NULL);
+
+    /* 3. Gas pressure (+ viscous) acceleration and energy rate. */
+    if (ng > 0) orc_accel(P, ng, gx, gv, ge, rho, acc, dedt);
+    if (acc_override) memcpy(acc, acc_override, sizeof(double) * (size_t)(dim * ng));
+
+    /* 4. Cell aggregates (Eqs. 17, 21), summed in sorted order. */
+    for (int64_t s = 0; s < ng; ++s) {
+        int64_t a = pg[s];
+        if (gfrozen && gfrozen[a]) continue;
+        int64_t c = kg[a];
+        cN[c] += 1.0;
+        for (int k = 0; k < dim; ++k) {
+            cv[3 * c + k] += gv[(int64_t)k * ng + a];
+            cA[3 * c + k] += acc[(int64_t)k * ng + a];
+        }
+    }
+    for (int64_t s = 0; s < nd; ++s) {
+        int64_t j = pd[s];
+        int64_t c = kd[j];
+        cL[c] += 1.0;
+        for (int k = 0; k < dim; ++k) cu[3 * c + k] += du[(int64_t)k * nd + j];
+        ct[c] += (P->tstar_mode == 1) ? 1.0 / tstop[j] : tstop[j];
+    }
+
+    /* 5. Per-cell implicit solve for the new mean velocities. */
+    double *ustar = (double *)calloc((size_t)(3 * ncells), sizeof(double));
+    double *vstar = (double *)calloc((size_t)(3 * ncells), sizeof(double));
+    double *eps_c = (double *)calloc((size_t)ncells, sizeof(double));
+    double *tst_c = (double *)calloc((size_t)ncells, sizeof(double));
+    if (!ustar || !vstar || !eps_c || !tst_c) {
+        free(ustar); free(vstar); free(eps_c); free(tst_c);
+        rc = ORC_E_OOM;
+        goto done;
+    }
+    int64_t ndrag = 0;
+    for (int64_t c = 0; c < ncells; ++c) {
+        if (cN[c] <= 0.0 || cL[c] <= 0.0) continue;
+        ++ndrag;
+        double N = cN[c], L = cL[c];
+        double eps = P->m_dust * L / (P->m_gas * N);                 /* Eq. 17 */
+        double tst = (P->tstar_mode == 1) ? L / ct[c] : ct[c] / L;   /* t*_stop */
+        eps_c[c] = eps;
+        tst_c[c] = tst;
+        for (int k = 0; k < dim; ++k) {
+            double vs = cv[3 * c + k] / N;                            /* Eq. 21 */
+            double us = cu[3 * c + k] / L;
+            double Abar = cA[3 * c + k] / N;
+            double w = vs - us;
+            double wn = (w + tau * Abar) / (1.0 + tau * (1.0 + eps) / tst);
+            double un = us + tau * g[k] + (tau / tst) * wn;
+            ustar[3 * c + k] = un;
+            vstar[3 * c + k] = un + wn;
+        }
+    }
+
+    /* 6. Particle velocities (Eqs. 19-20) and energies; 7. positions. */
+    for (int64_t a = 0; a < ng; ++a) {
+        if (gfrozen && gfrozen[a]) continue;
+        int64_t c = kg[a];
+        int drag = cN[c] > 0.0 && cL[c] > 0.0;
+        for (int k = 0; k < dim; ++k) {
+            double va = gv[(int64_t)k * ng + a];
+            double rhs = va + tau * (acc[(int64_t)k * ng + a] + g[k]);
+            double vn;
+            if (drag) {
+                double kg_ = eps_c[c] / tst_c[c];   /* K^/rho^_g */
+                vn = (rhs + tau * kg_ * ustar[3 * c + k]) / (1.0 + tau * kg_);
+            } else {
+                vn = rhs;
+            }
+            gv[(int64_t)k * ng + a] = vn;
+        }
+        if (P->eos == 1 && ge) ge[a] += tau * dedt[a];
+    }
+    for (int64_t j = 0; j < nd; ++j) {
+        int64_t c = kd[j];
+        int drag = cN[c] > 0.0 && cL[c] > 0.0;
+        for (int k = 0; k < dim; ++k) {
+            double uj = du[(int64_t)k * nd + j];
+            double rhs = uj + tau * g[k];
+            double un;
+            if (drag) {
+                double kd_ = 1.0 / tst_c[c];        /* K^/rho^_d */
+                un = (rhs + tau * kd_ * vstar[3 * c + k]) / (1.0 + tau * kd_);
+            } else {
+                un = rhs;
+            }
+            du[(int64_t)k * nd + j] = un;
+        }
+    }
+    for (int64_t a = 0; a < ng; ++a) {
+        if (gfrozen && gfrozen[a]) continue;
+        for (int k = 0; k < dim; ++k) {
+            double xn = gx[(int64_t)k * ng + a] + tau * gv[(int64_t)k * ng + a];
+            if (P->periodic[k]) xn = orc_wrap(xn, P->lo[k], P->hi[k]);
+            gx[(int64_t)k * ng + a] = xn;
+        }
+    }
+    for (int64_t j = 0; j < nd; ++j) {
+        for (int k = 0; k < dim; ++k) {
+            double xn = dx[(int64_t)k * nd + j] + tau * du[(int64_t)k * nd + j];
+            if (P->periodic[k]) xn = orc_wrap(xn, P->lo[k], P->hi[k]);
+            dx[(int64_t)k * nd + j] = xn;
+        }
+    }
+
+    if (out) {
+        if (out->rho_g) memcpy(out->rho_g, rho, sizeof(double) * (size_t)ng);
+        if (out->acc_g) memcpy(out->acc_g, acc, sizeof(double) * (size_t)(dim * ng));
+        if (out->dedt_g) memcpy(out->dedt_g, dedt, sizeof(double) * (size_t)ng);
+        if (out->keys_g) memcpy(out->keys_g, kg, sizeof(int64_t) * (size_t)ng);
+        if (out->keys_d) memcpy(out->keys_d, kd, sizeof(int64_t) * (size_t)nd);
+        if (out->perm_g) memcpy(out->perm_g, pg, sizeof(int64_t) * (size_t)ng);
+        if (out->perm_d) memcpy(out->perm_d, pd, sizeof(int64_t) * (size_t)nd);
+        if (out->cstart_g) memcpy(out->cstart_g, sg, sizeof(int64_t) * (size_t)(ncells + 1));
+        if (out->cstart_d) memcpy(out->cstart_d, sd, sizeof(int64_t) * (size_t)(ncells + 1));
+        out->n_drag_cells = ndrag;
+    }
+    free(ustar);
+    free(vstar);
+    free(eps_c);
+    free(tst_c);
+done:
+    free(kg); free(kd); free(pg); free(pd); free(sg); free(sd);
+    free(rho); free(acc); free(dedt);
+    free(cN); free(cL); free(cv); free(cu); free(cA); free(ct);
+    return rc;
+}

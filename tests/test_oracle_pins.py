@@ -1,0 +1,495 @@
+"""Pins of the FP64 oracle against closed forms, invariants and brute force.
+
+Each test ties the oracle to something other than itself: the exact solution
+of the continuum equations, an identity the scheme must satisfy exactly, a
+textbook routine (a dense linear solve, an exact Riemann solver, a matrix
+exponential), or an all-pairs search. Together they are meant to fail on a
+dropped term, a wrong sign or index, or a transposed operand anywhere in the
+oracle's step.
+"""
+import json
+import math
+import os
+
+import numpy as np
+import pytest
+from scipy import integrate
+
+import workloads
+from conftest import oracle_params
+
+GOLDEN = os.path.join(os.path.dirname(__file__), "golden")
+
+
+# --------------------------------------------------------------------------
+# Smoothing kernel
+# --------------------------------------------------------------------------
+@pytest.mark.parametrize("dim", [1, 2, 3])
+@pytest.mark.parametrize("h", [0.37, 1.0])
+def test_kernel_unit_integral(orc, dim, h):
+    """The M4 spline integrates to one over its support in d dimensions."""
+    shell = {1: lambda r: 2.0, 2: lambda r: 2.0 * math.pi * r, 3: lambda r: 4.0 * math.pi * r * r}[dim]
+    val, _ = integrate.quad(lambda r: orc.W(dim, h, r) * shell(r), 0.0, 2.0 * h, points=[h],
+                            epsabs=1e-13, epsrel=1e-13)
+    assert abs(val - 1.0) < 1e-10
+
+
+@pytest.mark.parametrize("dim", [1, 2, 3])
+def test_kernel_derivative_matches_finite_difference(orc, dim):
+    h = 0.7
+    for r in np.linspace(0.01, 1.99 * h, 37):
+        fd = (orc.W(dim, h, r + 1e-6) - orc.W(dim, h, r - 1e-6)) / 2e-6
+        assert abs(orc.dWdr(dim, h, r) - fd) < 1e-6 * (1.0 + abs(fd))
+    assert orc.W(dim, h, 2.0 * h) == 0.0 and orc.dWdr(dim, h, 2.0 * h) == 0.0
+
+
+# --------------------------------------------------------------------------
+# Cells and sorting
+# --------------------------------------------------------------------------
+@pytest.mark.parametrize("fp32", [0, 1])
+def test_binning_invariants(orc, fp32):
+    rng = np.random.default_rng(11)
+    p = orc.Params(dim=3, lo=(-0.5, 0.0, 2.0), hi=(0.5, 2.0, 3.0), periodic=(1, 0, 1), h=0.05,
+                   cell_size=0.1, m_gas=1.0, m_dust=1.0, decide_fp32=fp32)
+    x = np.stack([rng.uniform(-0.5, 0.5, 3000), rng.uniform(0.0, 2.0, 3000), rng.uniform(2.0, 3.0, 3000)])
+    if fp32:
+        x = x.astype(np.float32).astype(np.float64)
+    keys, perm, cstart = orc.bin_particles(p, x)
+    nc = orc.ncell(p)
+    assert nc == (10, 20, 10)
+    # sorted by (key, id)
+    sk = keys[perm]
+    assert np.all((np.diff(sk) > 0) | ((np.diff(sk) == 0) & (np.diff(perm) > 0)))
+    # cell starts are the bounds of equal-key runs
+    counts = np.bincount(keys, minlength=int(np.prod(nc)))
+    assert np.array_equal(np.diff(cstart), counts)
+    # every particle lies in the slab of its cell (to rounding)
+    c = np.stack([keys % nc[0], (keys // nc[0]) % nc[1], keys // (nc[0] * nc[1])])
+    for d in range(3):
+        w = (p.hi[d] - p.lo[d]) / nc[d]
+        lo = p.lo[d] + c[d] * w
+        assert np.all(x[d] >= lo - 1e-6) and np.all(x[d] < lo + w + 1e-6)
+
+
+# --------------------------------------------------------------------------
+# Neighbour sums: cell lists equal brute force
+# --------------------------------------------------------------------------
+def _random_gas(rng, dim, n, periodic):
+    lo = (0.0, -1.0, 0.5)[:dim]
+    hi = (1.0, 0.0, 1.5)[:dim]
+    x = np.stack([rng.uniform(lo[d], hi[d], n) for d in range(dim)])
+    v = rng.normal(size=(dim, n))
+    e = rng.uniform(1.0, 2.0, n)
+    return lo, hi, x, v, e
+
+
+@pytest.mark.parametrize("dim", [1, 2, 3])
+@pytest.mark.parametrize("periodic", [0, 1])
+@pytest.mark.parametrize("fp32", [0, 1])
+def test_cell_lists_equal_brute_force(orc, dim, periodic, fp32):
+    rng = np.random.default_rng(100 * dim + 10 * periodic + fp32)
+    n = {1: 400, 2: 900, 3: 1500}[dim]
+    lo, hi, x, v, e = _random_gas(rng, dim, n, periodic)
+    if fp32:
+        x = x.astype(np.float32).astype(np.float64)
+    h = {1: 0.01, 2: 0.04, 3: 0.09}[dim]
+    common = dict(dim=dim, lo=lo, hi=hi, periodic=(periodic,) * dim, h=h, cell_size=1.7 * h,
+                  m_gas=1.0 / n, m_dust=1.0, eos=1, gamma=1.4, av_alpha=1.0, av_beta=2.0,
+                  decide_fp32=fp32)
+    pc = orc.Params(brute=0, **common)
+    pb = orc.Params(brute=1, **common)
+    rc, cc, fc = orc.density(pc, x, pc.m_gas)
+    rb, cb, fb = orc.density(pb, x, pb.m_gas)
+    assert np.array_equal(cc, cb) and np.array_equal(fc, fb)
+    assert cc.min() >= 1 and cc.mean() > 3
+    np.testing.assert_allclose(rc, rb, rtol=1e-13, atol=0)
+    ac, dc = orc.accel(pc, x, v, e, rc)
+    ab, db = orc.accel(pb, x, v, e, rb)
+    scale = np.max(np.abs(ab))
+    assert np.max(np.abs(ac - ab)) < 1e-11 * scale
+    assert np.max(np.abs(dc - db)) < 1e-11 * np.max(np.abs(db))
+
+
+# --------------------------------------------------------------------------
+# Lattice properties of the SPH sums
+# --------------------------------------------------------------------------
+@pytest.mark.parametrize("dim,hf", [(1, 2.0), (2, 1.5), (3, 1.2)])
+def test_uniform_lattice_density_and_zero_force(orc, dim, hf):
+    """On a periodic unit-density lattice the summation density is 1 up to the
+    kernel's lattice error and the pressure force vanishes by symmetry."""
+    n1 = {1: 64, 2: 24, 3: 12}[dim]
+    ax = (np.arange(n1) + 0.5) / n1
+    grids = np.meshgrid(*([ax] * dim), indexing="ij")
+    x = np.stack([g.ravel() for g in grids])
+    n = x.shape[1]
+    p = orc.Params(dim=dim, lo=(0.0,) * dim, hi=(1.0,) * dim, periodic=(1,) * dim, h=hf / n1,
+                   cell_size=2 * hf / n1, m_gas=1.0 / n, m_dust=1.0)
+    rho, cnt, _ = orc.density(p, x, p.m_gas)
+    assert np.all(np.abs(rho - 1.0) < 0.03)
+    assert np.ptp(rho) < 1e-12
+    acc, _ = orc.accel(p, x, np.zeros_like(x), None, rho)
+    assert np.max(np.abs(acc)) < 1e-9
+
+
+def test_pressure_force_points_down_the_gradient(orc):
+    """Isothermal gas displaced by d(x0) = (a/k) cos(k x0): rho = 1/(1 - a sin k x0)
+    and A = -cs^2 rho_x / rho = -a k cos(k x0) / (1 - a sin k x0)^2 in the
+    continuum; the SPH force matches it to 1 % of a k at h = 2 dx."""
+    n, a, k = 400, 0.01, 2 * math.pi
+    w = workloads.dustywave(n=n, amp=a, h_factor=2.0)
+    p = oracle_params(w)
+    rho, _, _ = orc.density(p, w.gx, p.m_gas)
+    acc, _ = orc.accel(p, w.gx, w.gv, None, rho)
+    x0 = (np.arange(n) + 0.5) / n
+    exact = -(a * k * np.cos(k * x0)) / (1 - a * np.sin(k * x0)) ** 2
+    assert np.sqrt(np.mean((acc[0] - exact) ** 2)) < 0.01 * a * k
+
+
+def test_energy_rate_identity(orc):
+    """With artificial viscosity on, sum_a m (v_a . A_a + de_a/dt) = 0 exactly
+    (the symmetric pair terms conserve total energy of the semi-discrete system)."""
+    rng = np.random.default_rng(5)
+    n = 800
+    x = np.stack([rng.uniform(0, 1, n), rng.uniform(0, 1, n)])
+    v = rng.normal(size=(2, n))
+    e = rng.uniform(1.0, 3.0, n)
+    p = orc.Params(dim=2, lo=(0, 0), hi=(1, 1), periodic=(1, 1), h=0.05, cell_size=0.1,
+                   m_gas=1.0 / n, m_dust=1.0, eos=1, gamma=1.4, av_alpha=1.0, av_beta=2.0)
+    rho, _, _ = orc.density(p, x, p.m_gas)
+    acc, dedt = orc.accel(p, x, v, e, rho)
+    power = np.sum(p.m_gas * (np.sum(v * acc, axis=0) + dedt))
+    scale = np.sum(p.m_gas * np.abs(dedt))
+    assert abs(power) < 1e-12 * scale
+    # momentum of the pair forces is conserved as well
+    assert np.max(np.abs(np.sum(acc, axis=1))) < 1e-12 * np.sum(np.abs(acc))
+
+
+# --------------------------------------------------------------------------
+# The implicit drag-in-cell step (Eqs. 17-21)
+# --------------------------------------------------------------------------
+def _mixed_lattice(orc, n=60, seed=3, tstop=None, eps_mass=1.7):
+    """1D periodic gas and dust with random velocities and stopping times;
+    cells hold unequal numbers of gas and dust particles."""
+    rng = np.random.default_rng(seed)
+    gx = np.sort(rng.uniform(0, 1, n))[None, :]
+    dx = np.sort(rng.uniform(0, 1, int(n * 0.8)))[None, :]
+    gv = rng.normal(size=gx.shape)
+    du = rng.normal(size=dx.shape)
+    ts = rng.uniform(1e-3, 1e-1, dx.shape[1]) if tstop is None else np.full(dx.shape[1], tstop)
+    p = orc.Params(dim=1, lo=(0.0,), hi=(1.0,), periodic=(1,), h=0.02, cell_size=0.1,
+                   m_gas=1.0 / n, m_dust=eps_mass / n)
+    return p, orc.make_state(p, gx, gv, dx, du, ts)
+
+
+@pytest.mark.parametrize("tau", [1e-4, 1e-2, 10.0])
+def test_step_satisfies_implicit_cell_equations(orc, tau):
+    """The new velocities solve Eqs. 19-20 with the cell means of Eq. 21 at the
+    new time level, eps* from Eq. 17 and K*/rho*_g = eps*/t*, K*/rho*_d = 1/t*."""
+    p, s = _mixed_lattice(orc)
+    rng = np.random.default_rng(8)
+    A = rng.normal(size=s.gv.shape)
+    g = (0.3, 0.0, 0.0)
+    old = s.copy()
+    r = orc.step(p, s, tau, g, acc_override=A)
+    kg, kd = r.keys_g, r.keys_d
+    checked = 0
+    for c in np.unique(kg):
+        ga = np.where(kg == c)[0]
+        dj = np.where(kd == c)[0]
+        if len(ga) == 0 or len(dj) == 0:
+            # no drag: explicit update only
+            np.testing.assert_allclose(s.gv[0, ga], old.gv[0, ga] + tau * (A[0, ga] + g[0]), rtol=1e-13)
+            continue
+        eps = p.m_dust * len(dj) / (p.m_gas * len(ga))
+        tst = np.mean(old.tstop[dj])
+        vs_new = np.mean(s.gv[0, ga])
+        us_new = np.mean(s.du[0, dj])
+        res_g = (s.gv[0, ga] - old.gv[0, ga]) / tau - (A[0, ga] + g[0] - eps / tst * (s.gv[0, ga] - us_new))
+        res_d = (s.du[0, dj] - old.du[0, dj]) / tau - (g[0] + (vs_new - s.du[0, dj]) / tst)
+        scale = 1.0 + np.max(np.abs(s.gv[0, ga])) / tau + eps / tst * 10
+        assert np.max(np.abs(res_g)) < 1e-10 * scale
+        assert np.max(np.abs(res_d)) < 1e-10 * (1.0 + np.max(np.abs(s.du[0, dj])) / tau + 10 / tst)
+        checked += 1
+    assert checked >= 5
+    # dust with no gas in its cell: explicit update
+    for j in np.where(~np.isin(kd, kg))[0]:
+        assert abs(s.du[0, j] - (old.du[0, j] + tau * g[0])) < 1e-12
+
+
+def test_two_particle_cell_matches_dense_solve(orc):
+    """One gas and one dust particle per cell: the step is the 2x2 implicit
+    Euler system of Eqs. 19-20, solved here with numpy.linalg.solve."""
+    n = 10
+    gx = ((np.arange(n) + 0.5) / n)[None, :]
+    dx = ((np.arange(n) + 0.45) / n)[None, :]
+    rng = np.random.default_rng(2)
+    gv, du = rng.normal(size=(1, n)), rng.normal(size=(1, n))
+    ts = rng.uniform(1e-4, 1.0, n)
+    A = rng.normal(size=(1, n))
+    mg, md = 0.1, 0.37
+    p = orc.Params(dim=1, lo=(0.0,), hi=(1.0,), periodic=(1,), h=0.01, cell_size=0.1, m_gas=mg,
+                   m_dust=md)
+    s = orc.make_state(p, gx, gv, dx, du, ts)
+    tau, g = 0.05, -0.7
+    orc.step(p, s, tau, (g, 0, 0), acc_override=A)
+    eps = md / mg
+    for a in range(n):
+        t = ts[a]
+        M = np.array([[1 + tau * eps / t, -tau * eps / t], [-tau / t, 1 + tau / t]])
+        rhs = np.array([gv[0, a] + tau * (A[0, a] + g), du[0, a] + tau * g])
+        v_new, u_new = np.linalg.solve(M, rhs)
+        assert abs(s.gv[0, a] - v_new) < 1e-12 * (1 + abs(v_new))
+        assert abs(s.du[0, a] - u_new) < 1e-12 * (1 + abs(u_new))
+
+
+@pytest.mark.parametrize("tau_over_t", [1e-3, 1.0, 1e3, 1e6])
+def test_uniform_slip_relaxation_closed_form(orc, tau_over_t):
+    """Uniform gas and dust velocities, no pressure force, g = 0: the slip of
+    every cell obeys w_n = w_0 (1 + tau (1 + eps)/t_stop)^-n exactly, and the
+    mixture's momentum stays constant; for tau/t_stop -> 0 this tends to
+    w_0 exp(-(1 + eps) t / t_stop)."""
+    n = 40
+    x = ((np.arange(n) + 0.5) / n)[None, :]
+    t_stop = 1e-3
+    tau = tau_over_t * t_stop
+    mg, md = 1.0 / n, 0.5 / n
+    eps = md / mg
+    p = orc.Params(dim=1, lo=(0.0,), hi=(1.0,), periodic=(1,), h=0.5 / n, cell_size=0.1,
+                   m_gas=mg, m_dust=md)
+    s = orc.make_state(p, x, np.full((1, n), 0.4), x.copy(), np.full((1, n), -0.6), t_stop)
+    zero = np.zeros((1, n))
+    w0 = 1.0
+    mom0 = mg * s.gv.sum() + md * s.du.sum()
+    for k in range(1, 6):
+        orc.step(p, s, tau, acc_override=zero)
+        w = s.gv[0] - s.du[0]
+        exact = w0 * (1 + tau * (1 + eps) / t_stop) ** (-k)
+        assert np.max(np.abs(w - exact)) <= 1e-13 * abs(w0) + 1e-12 * abs(exact)
+        assert abs(mg * s.gv.sum() + md * s.du.sum() - mom0) < 1e-13
+    if tau_over_t <= 1e-3:
+        t = 5 * tau
+        assert abs(w[0] - w0 * math.exp(-(1 + eps) * t / t_stop)) < 2 * tau_over_t * w0
+
+
+@pytest.mark.parametrize("tau_over_t", [1e-3, 1.0, 1e2, 1e6])
+def test_terminal_slip_is_g_times_tstop(orc, tau_over_t):
+    """Gas held by a pressure force -(1+eps) g against gravity: the slip
+    converges to u - v = g t_stop for every tau/t_stop (the asymptotic limit),
+    following w_n = w_inf + (w_0 - w_inf) r^-n, r = 1 + tau (1+eps)/t_stop."""
+    n = 30
+    x = ((np.arange(n) + 0.5) / n)[None, :]
+    t_stop = 2e-3
+    tau = tau_over_t * t_stop
+    mg, md = 1.0 / n, 1.0 / n
+    eps = md / mg
+    g = -1.0
+    p = orc.Params(dim=1, lo=(0.0,), hi=(1.0,), periodic=(1,), h=0.5 / n, cell_size=0.1,
+                   m_gas=mg, m_dust=md)
+    s = orc.make_state(p, x, np.zeros((1, n)), x.copy(), np.zeros((1, n)), t_stop)
+    A = np.full((1, n), -(1 + eps) * g)
+    r = 1 + tau * (1 + eps) / t_stop
+    w_inf = -g * t_stop
+    for k in range(1, 8):
+        orc.step(p, s, tau, (g, 0, 0), acc_override=A)
+        w = s.gv[0] - s.du[0]
+        exact = w_inf + (0.0 - w_inf) * r ** (-k)
+        # the update adds tau g and (tau/t_stop) w', which cancel to O(w): binary64
+        # rounding of those terms bounds the attainable accuracy
+        bound = 1e-12 * abs(w_inf) + 1e-14 * k * tau * (abs(g) + abs(A[0, 0]))
+        assert np.max(np.abs(w - exact)) < bound
+    if tau_over_t >= 1e2:
+        assert np.max(np.abs((s.du[0] - s.gv[0]) - g * t_stop)) < 1e-6 * abs(g * t_stop)
+
+
+def test_cell_momentum_conserved_by_drag(orc):
+    """With no pressure force and g = 0, each cell's momentum m_g sum v + m_d sum u
+    is unchanged by the drag step (Sec. 2.3)."""
+    p, s = _mixed_lattice(orc, seed=21)
+    old = s.copy()
+    r = orc.step(p, s, 0.7, acc_override=np.zeros_like(s.gv))
+    for c in np.unique(np.concatenate([r.keys_g, r.keys_d])):
+        ga = r.keys_g == c
+        dj = r.keys_d == c
+        before = p.m_gas * old.gv[0, ga].sum() + p.m_dust * old.du[0, dj].sum()
+        after = p.m_gas * s.gv[0, ga].sum() + p.m_dust * s.du[0, dj].sum()
+        assert abs(after - before) < 1e-14 * (1 + abs(before)) * 10
+
+
+def test_total_momentum_conserved_with_pressure(orc):
+    """Periodic 2D gas and dust with pressure on and g = 0: the total momentum
+    is conserved to rounding (antisymmetric pair forces, conservative drag)."""
+    rng = np.random.default_rng(4)
+    n = 900
+    gx = rng.uniform(0, 1, (2, n))
+    dx = rng.uniform(0, 1, (2, n))
+    p = orc.Params(dim=2, lo=(0, 0), hi=(1, 1), periodic=(1, 1), h=0.05, cell_size=0.1,
+                   m_gas=1.0 / n, m_dust=0.8 / n)
+    s = orc.make_state(p, gx, rng.normal(size=(2, n)), dx, rng.normal(size=(2, n)),
+                       rng.uniform(1e-3, 1e-1, n))
+    m0 = p.m_gas * s.gv.sum(axis=1) + p.m_dust * s.du.sum(axis=1)
+    orc.step(p, s, 1e-3)
+    m1 = p.m_gas * s.gv.sum(axis=1) + p.m_dust * s.du.sum(axis=1)
+    assert np.max(np.abs(m1 - m0)) < 1e-12
+
+
+def test_galilean_invariance(orc):
+    """Adding a constant V to every velocity shifts every new velocity by V."""
+    w = workloads.box3d(nside=8, precision=1)
+    p = oracle_params(w)
+    s1 = orc.make_state(p, w.gx, w.gv, w.dx, w.du, w.tstop)
+    V = np.array([[0.3], [-0.2], [0.1]])
+    s2 = orc.make_state(p, w.gx, w.gv + V, w.dx, w.du + V, w.tstop)
+    r1 = orc.step(p, s1, w.tau)
+    r2 = orc.step(p, s2, w.tau)
+    np.testing.assert_allclose(r1.rho_g, r2.rho_g, rtol=1e-14)
+    assert np.max(np.abs(s2.gv - (s1.gv + V))) < 1e-12
+    assert np.max(np.abs(s2.du - (s1.du + V))) < 1e-12
+
+
+def test_frozen_particles_neither_move_nor_drag(orc):
+    w = workloads.dustyshock(n_left=160, n_right=20, precision=1)
+    p = oracle_params(w)
+    s = orc.make_state(p, w.gx, w.gv, w.dx, w.du, w.tstop, ge=w.ge, frozen=w.frozen)
+    fr = w.frozen == 1
+    x0, e0 = s.gx[:, fr].copy(), s.ge[fr].copy()
+    for _ in range(3):
+        orc.step(p, s, w.tau)
+    assert np.array_equal(s.gx[:, fr], x0) and np.array_equal(s.ge[fr], e0)
+    assert np.all(s.gv[:, fr] == 0.0)
+
+
+@pytest.mark.parametrize("mode", [0, 1])
+def test_tstar_means_agree_for_equal_stopping_times(orc, mode):
+    p, s = _mixed_lattice(orc, tstop=3e-3)
+    p.tstar_mode = mode
+    p0, s0 = _mixed_lattice(orc, tstop=3e-3)
+    A = np.zeros_like(s.gv)
+    orc.step(p, s, 1e-2, acc_override=A)
+    orc.step(p0, s0, 1e-2, acc_override=A)
+    np.testing.assert_allclose(s.gv, s0.gv, rtol=1e-13, atol=1e-15)
+
+
+def test_max_dt_special_cases(orc):
+    p = orc.Params(dim=2, lo=(0, 0), hi=(1, 1), periodic=(1, 1), h=0.02, cell_size=0.04,
+                   m_gas=1.0, m_dust=1.0, cs=2.0)
+    v = np.zeros((2, 5))
+    assert orc.max_dt(p, v, cfl=0.3) == pytest.approx(0.3 * 0.02 / 2.0, rel=1e-15)
+    v[:, 3] = (6.0, 8.0)  # |v| = 10 > cs
+    assert orc.max_dt(p, v, cfl=0.3) == pytest.approx(0.3 * 0.02 / 10.0, rel=1e-15)
+    fr = np.array([0, 0, 0, 1, 0], np.uint8)  # frozen particles do not count
+    assert orc.max_dt(p, v, frozen=fr, cfl=0.3) == pytest.approx(0.3 * 0.02 / 2.0, rel=1e-15)
+
+
+# --------------------------------------------------------------------------
+# Test problems with exact solutions (Sec. 3)
+# --------------------------------------------------------------------------
+def test_dispersion_cubic_matches_linear_operator():
+    from oracle import analytic
+    for ts, eps in [(1e-3, 1.0), (0.05, 0.3), (2.0, 3.0)]:
+        k = 2 * math.pi
+        M = analytic.wave_matrix(k, 1.0, 1.0, eps, ts)
+        ev = np.linalg.eigvals(M)
+        rt = analytic.dispersion_roots(k, 1.0, ts, eps)
+        for r in rt:  # same multiset of roots
+            assert np.min(np.abs(ev - r)) < 1e-9 * (1.0 + abs(r))
+        for e in ev:
+            assert np.min(np.abs(rt - e)) < 1e-9 * (1.0 + abs(e))
+    # strongly coupled limit: phase speed cs / sqrt(1 + eps)
+    rt = analytic.dispersion_roots(2 * math.pi, 1.0, 1e-7, 1.0)
+    osc = rt[np.argmax(np.abs(rt.imag))]
+    assert abs(abs(osc.imag) / (2 * math.pi) - 1 / math.sqrt(2)) < 1e-6
+
+
+def _wave_error(orc, n, hf, with_dust=True, T=0.72):
+    from oracle import analytic
+    w = workloads.dustywave(n=n, h_factor=hf)
+    p = oracle_params(w)
+    if not with_dust:
+        p.m_dust = 1e-300
+    s = orc.make_state(p, w.gx, w.gv, w.dx, w.du, w.tstop)
+    ns = int(round(T / w.tau))
+    for _ in range(ns):
+        orc.step(p, s, w.tau)
+    t = ns * w.tau
+    rd = 1.0 if with_dust else 1e-300
+    m = w.meta
+    _, v, _ = analytic.dusty_wave(s.gx[0], t, m["k"], 1.0, 1.0, rd, m["tstop_scalar"], m["amp"], m["amp"], m["amp"])
+    _, _, u = analytic.dusty_wave(s.dx[0], t, m["k"], 1.0, 1.0, rd, m["tstop_scalar"], m["amp"], m["amp"], m["amp"])
+    return (np.sqrt(np.mean((s.gv[0] - v) ** 2)) / m["amp"],
+            np.sqrt(np.mean((s.du[0] - u) ** 2)) / m["amp"])
+
+
+def test_gas_sound_wave_matches_exact_solution(orc):
+    """Dust-free isothermal sound wave (h = 2 dx): the SPH pressure force
+    reproduces the exact travelling wave to under 2 % of its amplitude."""
+    eg, _ = _wave_error(orc, 200, 2.0, with_dust=False)
+    assert eg < 0.02
+
+
+def test_dusty_wave_converges_to_exact_solution(orc):
+    """Dustywave (Sec. 3) with t_stop = 1e-3, tau/t_stop = 3.6-0.9, cell = 2h,
+    h = 2 dx: gas and dust velocities converge to the exact linear solution at
+    second order in resolution (error ratio > 3 per doubling, 2 would be first order)."""
+    errs = [_wave_error(orc, n, 2.0) for n in (200, 400, 800)]
+    for (g0, d0), (g1, d1) in zip(errs, errs[1:]):
+        assert g0 / g1 > 3.0 and d0 / d1 > 3.0
+    assert errs[-1][0] < 0.015 and errs[-1][1] < 0.015
+
+
+def _run_shock(orc, w, p, T, tau):
+    s = orc.make_state(p, w.gx, w.gv, w.dx, w.du, w.tstop, ge=w.ge, frozen=w.frozen)
+    ns = int(round(T / tau))
+    for _ in range(ns):
+        orc.step(p, s, tau)
+    return s, ns * tau
+
+
+def test_sod_shock_tube_converges(orc):
+    """Dust-free adiabatic Sod tube (gamma = 1.4, artificial viscosity on, wall
+    particles frozen): density and velocity converge to the exact Riemann
+    solution at first order in resolution."""
+    from oracle import analytic
+    errs = []
+    for nl in (400, 800, 1600):
+        w = workloads.dustyshock(n_left=nl, n_right=nl // 8, with_dust=False, precision=1)
+        p = oracle_params(w)
+        s, t = _run_shock(orc, w, p, 0.1, w.tau)
+        fl = s.frozen == 0
+        r, u, _ = analytic.sod_exact(s.gx[0][fl], t, 0.5, 1.0, 0.0, 1.0, 0.125, 0.0, 0.1, 1.4)
+        rho, _, _ = orc.density(p, s.gx, p.m_gas)
+        errs.append((np.mean(np.abs(rho[fl] - r)), np.mean(np.abs(s.gv[0][fl] - u))))
+    for (r0, u0), (r1, u1) in zip(errs, errs[1:]):
+        assert r0 / r1 > 1.7 and u0 / u1 > 1.7
+    assert errs[-1][0] < 0.002 and errs[-1][1] < 0.004
+
+
+def test_coupled_isothermal_dusty_shock_converges(orc):
+    """Dustyshock with t_stop = 1e-6 (tau/t_stop ~ 1e2): gas and dust move
+    together as one isothermal fluid with sound speed cs/sqrt(1+eps) and density
+    (1+eps) rho_g, whose exact Riemann solution the run approaches."""
+    from oracle import analytic
+    errs = []
+    for nl in (400, 800, 1600):
+        w = workloads.dustyshock(n_left=nl, n_right=nl // 8, eos=0, tstop=1e-6, precision=1)
+        p = oracle_params(w)
+        tau = 0.3 * p.h
+        s, t = _run_shock(orc, w, p, 0.1, tau)
+        fl = s.frozen == 0
+        a = 1.0 / math.sqrt(2.0)
+        r, u = analytic.isothermal_riemann(s.gx[0][fl], t, 0.5, 2.0, 0.0, 0.25, 0.0, a)
+        _, ud = analytic.isothermal_riemann(s.dx[0], t, 0.5, 2.0, 0.0, 0.25, 0.0, a)
+        rho, _, _ = orc.density(p, s.gx, p.m_gas)
+        errs.append((np.mean(np.abs(2 * rho[fl] - r)), np.mean(np.abs(s.gv[0][fl] - u)),
+                     np.mean(np.abs(s.du[0] - ud))))
+    for e0, e1 in zip(errs, errs[1:]):
+        assert all(a0 / a1 > 1.5 for a0, a1 in zip(e0, e1))
+    assert errs[-1][1] < 0.01 and errs[-1][2] < 0.01
+
+
+def test_paper_parameters_fix_tstop():
+    """Eq. 7 defines K = rho_d / t_stop; with K = 500 and rho_d = rho_g = 1
+    (Eq. 22) the stopping time is the 0.002 the Dustywave text quotes."""
+    with open(os.path.join(GOLDEN, "paper_parameters.json")) as f:
+        g = json.load(f)
+    rho_d = 1.0 * g["dust_to_gas_ratio"]
+    assert rho_d / g["drag_coefficient_K"] == pytest.approx(g["dustywave_tstop_stated"], rel=1e-12)
