@@ -1,0 +1,195 @@
+/*
+ * tfsph.h - C ABI of the GB300 SPH-IDIC library.
+ *
+ * One time step of two-fluid smoothed particle hydrodynamics (TFSPH) for a
+ * gas-dust mixture whose stiff interphase drag is solved implicitly per Euler
+ * cell ("drag in cell", SPH-IDIC), after Stoyanovskaya, Glushko, Snytnikov
+ * and Snytnikov, arXiv:1908.01682:
+ *   - carrier (gas) and dispersed (dust) phases as two particle sets,
+ *     momentum equations in the K form of Eq. 7, drag f = rho_d (v-u)/t_stop
+ *     (Eq. 3);
+ *   - gas pressure acceleration as the symmetric SPH sum of the first term of
+ *     Eq. 19, with the summation density rho^n;
+ *   - the domain split into disjoint cells holding N gas and L dust
+ *     particles (Sec. 2.3), eps* = m_d L / (m_g N) (Eq. 17), K* with
+ *     K* / rho*_g = eps* / t*_stop and K* / rho*_d = 1 / t*_stop (Eq. 18);
+ *   - the implicit first-order update of Eqs. 19-20 against the new cell
+ *     means of Eq. 21, which conserves each cell's momentum.
+ *
+ * Conventions for every call:
+ *   - Return value: TFSPH_OK (0) or one of the TFSPH_E_* codes below; no call
+ *     aborts, throws or traps the GPU. tfsph_last_error() gives a message.
+ *   - Floating-point arrays are of the context's precision: float for
+ *     TFSPH_FP32, double for TFSPH_FP64.
+ *   - mem_kind tells whether a pointer is host memory (TFSPH_MEM_HOST) or
+ *     device memory of the current CUDA device (TFSPH_MEM_DEVICE).
+ *   - Ownership: the library deep-copies inputs and owns all its device state;
+ *     the caller owns every output buffer. Pointers are only read during the
+ *     call (asynchronously on the context's stream for device pointers, so the
+ *     caller keeps them alive until that stream has reached the call).
+ *   - Concurrency: a context is used from one host thread at a time; all its
+ *     GPU work is issued on the stream given to tfsph_set_stream (default:
+ *     the legacy default stream). tfsph_step makes no host synchronisation.
+ *   - Particle identity: particle i of the arrays given to tfsph_init has id
+ *     i. Inside the library particles are kept sorted by (cell key, id).
+ */
+#ifndef TFSPH_H
+#define TFSPH_H
+
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+/* status codes */
+#define TFSPH_OK              0
+#define TFSPH_E_INVALID_ARG   1  /* bad parameter, size, pointer or enum */
+#define TFSPH_E_NONFINITE     2  /* NaN/Inf input, or t_stop <= 0 */
+#define TFSPH_E_OUT_OF_DOMAIN 3  /* a moving particle outside [lo, hi) at set-up */
+#define TFSPH_E_CUDA          4  /* a CUDA runtime call failed */
+#define TFSPH_E_OOM           5  /* device or host allocation failed */
+#define TFSPH_E_INTERNAL      6  /* a device-side consistency check failed */
+
+#define TFSPH_MEM_HOST   0
+#define TFSPH_MEM_DEVICE 1
+
+#define TFSPH_FP32 0  /* float state and pair sums */
+#define TFSPH_FP64 1  /* double everywhere */
+
+#define TFSPH_EOS_ISOTHERMAL 0  /* p = cs^2 rho */
+#define TFSPH_EOS_ADIABATIC  1  /* p = (gamma - 1) rho e, with an energy equation */
+
+#define TFSPH_KERNEL_CUBIC 0    /* M4 cubic spline, support 2h */
+
+#define TFSPH_TSTAR_ARITHMETIC 0 /* t*_stop = mean of the cell's t_j */
+#define TFSPH_TSTAR_HARMONIC   1 /* t*_stop = L / sum 1/t_j */
+
+#define TFSPH_CELL_ACC_FP32 0   /* per-cell sums and drag solve in float */
+#define TFSPH_CELL_ACC_FP64 1   /* per-cell sums and drag solve in double */
+
+/* fields for tfsph_fields; vector fields are written component-major, out[k*n + i] */
+#define TFSPH_FIELD_POS_G    0  /* dim x n_gas */
+#define TFSPH_FIELD_VEL_G    1  /* dim x n_gas */
+#define TFSPH_FIELD_ENERGY_G 2  /* n_gas, specific internal energy (adiabatic) */
+#define TFSPH_FIELD_RHO_G    3  /* n_gas, summation density at the current positions */
+#define TFSPH_FIELD_POS_D    4  /* dim x n_dust */
+#define TFSPH_FIELD_VEL_D    5  /* dim x n_dust */
+#define TFSPH_FIELD_TSTOP_D  6  /* n_dust */
+#define TFSPH_FIELD_RHO_D    7  /* n_dust, dust summation density at the current positions */
+
+#define TFSPH_ORDER_ORIGINAL 0  /* out[i] belongs to the particle with id i */
+#define TFSPH_ORDER_CELL     1  /* out[s] belongs to storage slot s (sorted by cell, id) */
+
+/* debug exports for tfsph_debug; all refer to the binning of the current positions */
+#define TFSPH_DEBUG_KEYS_G       0  /* uint32[n_gas]  cell key per storage slot */
+#define TFSPH_DEBUG_KEYS_D       1  /* uint32[n_dust] */
+#define TFSPH_DEBUG_PERM_G       2  /* uint32[n_gas]  particle id per storage slot */
+#define TFSPH_DEBUG_PERM_D       3  /* uint32[n_dust] */
+#define TFSPH_DEBUG_CSTART_G     4  /* uint32[n_cells + 1] first slot of each cell */
+#define TFSPH_DEBUG_CSTART_D     5  /* uint32[n_cells + 1] */
+#define TFSPH_DEBUG_NEIGH_COUNT  6  /* int32[n_gas] gas neighbours (r < 2h, self included) */
+#define TFSPH_DEBUG_NEIGH_FPRINT 7  /* uint64[n_gas] sum over neighbours of (id+1)*0x9E3779B97F4A7C15 */
+#define TFSPH_DEBUG_ACC_G        8  /* T[dim x n_gas] pressure acceleration of the last step, storage order */
+
+typedef struct tfsph_ctx tfsph_ctx;
+
+/* Problem parameters. Cells form a uniform grid from lo with
+ * n_d = max(1, floor((hi_d - lo_d) / cell_size)) cells along axis d; the
+ * same cells serve the drag (Sec. 2.3) and the neighbour search. */
+typedef struct {
+    int32_t dim;          /* 1, 2 or 3 */
+    int32_t precision;    /* TFSPH_FP32 | TFSPH_FP64 */
+    int32_t kernel;       /* TFSPH_KERNEL_CUBIC */
+    int32_t eos;          /* TFSPH_EOS_* */
+    int32_t periodic[3];  /* 1 = periodic axis, 0 = open axis (walls are frozen gas particles) */
+    int32_t tstar_mode;   /* TFSPH_TSTAR_* */
+    int32_t cell_acc;     /* TFSPH_CELL_ACC_*; forced to FP64 when precision is FP64 */
+    int32_t reserved;     /* must be 0 */
+    double lo[3], hi[3];  /* box; periodic axes need hi - lo >= 4h */
+    double h;             /* smoothing length (> 0), kernel support 2h */
+    double cell_size;     /* requested cell edge (> 0) */
+    double m_gas, m_dust; /* particle masses (> 0) */
+    double cs;            /* isothermal sound speed (> 0) */
+    double gamma;         /* adiabatic index (> 1 when adiabatic) */
+    double av_alpha, av_beta; /* Monaghan artificial viscosity (>= 0; 0, 0 = off) */
+} tfsph_params;
+
+typedef struct {
+    int64_t n_gas, n_dust;
+    int32_t n_cells[3];
+    int32_t reach[3];      /* neighbour-search reach in cells per axis */
+    int64_t n_cells_total;
+    int64_t steps;         /* steps taken since init or the last set_state */
+    int64_t device_bytes;  /* device memory held by the context */
+} tfsph_info_t;
+
+/* Create a context from a particle state (Sec. 2.3 set-up).
+ *   gas[]:  2*dim arrays of n_gas values, x_0..x_{dim-1}, v_0..v_{dim-1},
+ *           then, for TFSPH_EOS_ADIABATIC, the specific energy e.
+ *   dust[]: 2*dim + 1 arrays of n_dust values, x.., u.., then t_stop (> 0).
+ *   frozen: nullable, n_gas bytes; nonzero marks a wall particle that enters
+ *           the SPH sums but never moves and takes no part in the drag.
+ * Moving particles must lie in [lo, hi) on every axis. n_gas, n_dust may be
+ * 0 and must be < 2^31. Errors: INVALID_ARG, NONFINITE, OUT_OF_DOMAIN, OOM,
+ * CUDA. On error *out is NULL. */
+int tfsph_init(tfsph_ctx **out, const tfsph_params *p,
+               const void *const *gas, int64_t n_gas,
+               const void *const *dust, int64_t n_dust,
+               const uint8_t *frozen, int mem_kind);
+
+/* Replace the whole particle state (same counts and layout as tfsph_init). */
+int tfsph_set_state(tfsph_ctx *c, const void *const *gas, const void *const *dust,
+                    const uint8_t *frozen, int mem_kind);
+
+/* Use `stream` (a cudaStream_t, may be NULL for the default stream) for all
+ * later work of this context. */
+int tfsph_set_stream(tfsph_ctx *c, void *stream);
+
+/* Advance the mixture by one step tau (> 0) under gravity g[3] (Eqs. 19-21):
+ * bin both phases into cells, gas summation density and pressure force,
+ * per-cell eps*, t*_stop and mean velocities, implicit drag, new velocities
+ * and positions x' = x + tau v' (periodic axes wrapped).
+ *   t_stop: nullable; n_dust new stopping times in id order (memory of
+ *           mem_kind) replacing the resident ones from this step on.
+ * Asynchronous: a bad value inside a device t_stop array is reported by the
+ * next tfsph_sync / tfsph_fields as NONFINITE. */
+int tfsph_step(tfsph_ctx *c, double tau, const void *t_stop, int mem_kind, const double g[3]);
+
+/* Courant step (Eq. 4): *tau_out = cfl * h / max over moving gas of
+ * max(|v_a|, c_a). Synchronises the stream. */
+int tfsph_max_dt(tfsph_ctx *c, double cfl, double *tau_out);
+
+/* Copy one field (TFSPH_FIELD_*) into `out` in the given order
+ * (TFSPH_ORDER_*). Density fields are computed at the current positions.
+ * Synchronises the stream when `out` is host memory. */
+int tfsph_fields(tfsph_ctx *c, int field, void *out, int mem_kind, int order);
+
+/* Debug exports (TFSPH_DEBUG_*), for tests. Synchronises for host output. */
+int tfsph_debug(tfsph_ctx *c, int what, void *out, int mem_kind);
+
+/* Sizes and counters of a context. */
+int tfsph_info(const tfsph_ctx *c, tfsph_info_t *out);
+
+/* Wait for the context's stream and report any error raised on the device
+ * since the last call (NONFINITE for bad t_stop values, INTERNAL otherwise). */
+int tfsph_sync(tfsph_ctx *c);
+
+/* Message of the last error of `c` (or of the last failed tfsph_init when c
+ * is NULL). The string lives until the next call on the same context. */
+const char *tfsph_last_error(const tfsph_ctx *c);
+
+/* Static name of a status code. */
+const char *tfsph_status_string(int code);
+
+/* Free the context and its device memory (NULL is allowed). */
+void tfsph_destroy(tfsph_ctx *c);
+
+/* Library version, major * 10000 + minor * 100 + patch. */
+int tfsph_version(void);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* TFSPH_H */

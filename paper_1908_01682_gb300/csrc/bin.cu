@@ -1,0 +1,500 @@
+// Binning of both phases into cells (the decomposition into disjoint volumes
+// of Sec. 2.3) and the data movement around it.
+//
+// Sort by (cell key, particle id), in four passes over both phases at once:
+//   1. count   : count[key]++ per particle (atomics; the counts are exact).
+//   2. scan    : start = exclusive prefix sum of count (reduce / top / down),
+//                start[ncells] = n. These are the cell ranges.
+//   3. scatter : slot = start[key] + (atomicSub(count[key]) - 1); the order
+//                inside a cell is arbitrary here and count returns to zero.
+//   4. rank + gather : the rank of a particle inside its cell is the number
+//                of the cell's particles with a smaller id, so the final slot
+//                start[key] + rank is unique and deterministic; the particle's
+//                state is copied there (double buffer).
+// Also: packing of user arrays, field export, t_stop updates, input checks
+// and the Courant speed reduction.
+#include "tfsph_internal.cuh"
+
+namespace tfsph {
+namespace {
+
+template <class T, int DIM>
+__global__ void k_keys(Geo<T> G, const V4<T> *__restrict__ pos, int n, uint32_t *__restrict__ key)
+{
+    const int i = blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= n) return;
+    const V4<T> p = pos[i];
+    key[i] = cell_key<T, DIM>(G, p.x, p.y, p.z);
+}
+
+__global__ void k_count(const uint32_t *__restrict__ kg, int ng, uint32_t *__restrict__ cg,
+                        const uint32_t *__restrict__ kd, int nd, uint32_t *__restrict__ cd)
+{
+    const int i = blockIdx.x * blockDim.x + threadIdx.x;
+    if (i < ng) atomicAdd(&cg[kg[i]], 1u);
+    else if (i < ng + nd) atomicAdd(&cd[kd[i - ng]], 1u);
+}
+
+// Block-wide exclusive scan of one value per thread; returns the block total.
+__device__ __forceinline__ uint32_t block_exclusive_scan(uint32_t v, uint32_t &excl)
+{
+    __shared__ uint32_t warp_tot[kScanThreads / 32];
+    const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
+    uint32_t x = v;
+#pragma unroll
+    for (int o = 1; o < 32; o <<= 1) {
+        const uint32_t y = __shfl_up_sync(0xffffffffu, x, o);
+        if (lane >= o) x += y;
+    }
+    if (lane == 31) warp_tot[wid] = x;
+    __syncthreads();
+    if (wid == 0) {
+        uint32_t t = lane < kScanThreads / 32 ? warp_tot[lane] : 0u;
+#pragma unroll
+        for (int o = 1; o < 32; o <<= 1) {
+            const uint32_t y = __shfl_up_sync(0xffffffffu, t, o);
+            if (lane >= o) t += y;
+        }
+        if (lane < kScanThreads / 32) warp_tot[lane] = t;  // inclusive warp totals
+    }
+    __syncthreads();
+    const uint32_t before = wid > 0 ? warp_tot[wid - 1] : 0u;
+    excl = before + x - v;
+    const uint32_t total = warp_tot[kScanThreads / 32 - 1];
+    __syncthreads();
+    return total;
+}
+
+// blockIdx.y selects the phase (0 gas, 1 dust).
+__global__ void __launch_bounds__(kScanThreads)
+k_scan_reduce(const uint32_t *__restrict__ cg, const uint32_t *__restrict__ cd, uint32_t ncells,
+              uint32_t *__restrict__ bsum, uint32_t nblk)
+{
+    const uint32_t *cnt = blockIdx.y == 0 ? cg : cd;
+    const uint32_t base = blockIdx.x * kScanTile + threadIdx.x * kScanItems;
+    uint32_t s = 0;
+#pragma unroll
+    for (int k = 0; k < kScanItems; ++k) {
+        const uint32_t c = base + k;
+        if (c < ncells) s += cnt[c];
+    }
+    uint32_t excl;
+    const uint32_t tot = block_exclusive_scan(s, excl);
+    if (threadIdx.x == 0) bsum[blockIdx.y * nblk + blockIdx.x] = tot;
+}
+
+// One block per phase: exclusive scan of the nblk block totals in place.
+__global__ void __launch_bounds__(kScanThreads) k_scan_top(uint32_t *__restrict__ bsum, uint32_t nblk)
+{
+    uint32_t *b = bsum + blockIdx.x * nblk;
+    uint32_t carry = 0;
+    for (uint32_t base = 0; base < nblk; base += kScanThreads) {
+        const uint32_t i = base + threadIdx.x;
+        const uint32_t v = i < nblk ? b[i] : 0u;
+        uint32_t excl;
+        const uint32_t tot = block_exclusive_scan(v, excl);
+        if (i < nblk) b[i] = carry + excl;
+        carry += tot;
+    }
+}
+
+__global__ void __launch_bounds__(kScanThreads)
+k_scan_down(const uint32_t *__restrict__ cg, const uint32_t *__restrict__ cd, uint32_t ncells,
+            const uint32_t *__restrict__ bsum, uint32_t nblk, uint32_t *__restrict__ sg,
+            uint32_t *__restrict__ sd, uint32_t ng, uint32_t nd)
+{
+    const uint32_t *cnt = blockIdx.y == 0 ? cg : cd;
+    uint32_t *st = blockIdx.y == 0 ? sg : sd;
+    const uint32_t base = blockIdx.x * kScanTile + threadIdx.x * kScanItems;
+    uint32_t v[kScanItems];
+    uint32_t s = 0;
+#pragma unroll
+    for (int k = 0; k < kScanItems; ++k) {
+        const uint32_t c = base + k;
+        v[k] = c < ncells ? cnt[c] : 0u;
+        s += v[k];
+    }
+    uint32_t excl;
+    block_exclusive_scan(s, excl);
+    uint32_t run = bsum[blockIdx.y * nblk + blockIdx.x] + excl;
+#pragma unroll
+    for (int k = 0; k < kScanItems; ++k) {
+        const uint32_t c = base + k;
+        if (c < ncells) st[c] = run;
+        run += v[k];
+    }
+    if (blockIdx.x == 0 && threadIdx.x == 0) st[ncells] = blockIdx.y == 0 ? ng : nd;
+}
+
+// Takes one slot of cell k; a count that is already zero or a slot past the
+// end means the counts and keys disagree: flagged, nothing written.
+__device__ __forceinline__ void scatter_one(uint32_t i, const uint32_t *__restrict__ key,
+                                            const uint32_t *__restrict__ id, uint32_t *__restrict__ cnt,
+                                            const uint32_t *__restrict__ start, uint32_t *__restrict__ src,
+                                            uint32_t *__restrict__ tid, uint32_t n, int *err)
+{
+    const uint32_t k = key[i];
+    const uint32_t old = atomicSub(&cnt[k], 1u);
+    const uint32_t slot = start[k] + old - 1u;
+    if (old == 0u || slot >= n) {
+        atomicAdd(&cnt[k], 1u);
+        atomicOr(err, kErrInternal);
+        return;
+    }
+    src[slot] = i;
+    tid[slot] = id[i] & kIdMask;
+}
+
+__global__ void k_scatter(const uint32_t *__restrict__ kg, const uint32_t *__restrict__ idg,
+                          uint32_t *__restrict__ cg, const uint32_t *__restrict__ sg, uint32_t *__restrict__ srcg,
+                          uint32_t *__restrict__ tidg, int ng, const uint32_t *__restrict__ kd,
+                          const uint32_t *__restrict__ idd, uint32_t *__restrict__ cd,
+                          const uint32_t *__restrict__ sd, uint32_t *__restrict__ srcd,
+                          uint32_t *__restrict__ tidd, int nd, int *err)
+{
+    const int i = blockIdx.x * blockDim.x + threadIdx.x;
+    if (i < ng) scatter_one((uint32_t)i, kg, idg, cg, sg, srcg, tidg, (uint32_t)ng, err);
+    else if (i < ng + nd) scatter_one((uint32_t)(i - ng), kd, idd, cd, sd, srcd, tidd, (uint32_t)nd, err);
+}
+
+template <class T>
+__device__ __forceinline__ void rank_move(uint32_t s, const uint32_t *__restrict__ key,
+                                          const uint32_t *__restrict__ start, const uint32_t *__restrict__ src,
+                                          const uint32_t *__restrict__ tid, const V4<T> *__restrict__ pos,
+                                          const V4<T> *__restrict__ vel, const uint32_t *__restrict__ id,
+                                          V4<T> *__restrict__ opos, V4<T> *__restrict__ ovel,
+                                          uint32_t *__restrict__ oid, uint32_t n, int *err)
+{
+    const uint32_t i = src[s];
+    if (i >= n) {  // a slot the scatter did not fill (flagged there too)
+        atomicOr(err, kErrInternal);
+        return;
+    }
+    const uint32_t k = key[i];
+    const uint32_t b = start[k], e = start[k + 1];
+    uint32_t d = b;
+    if (e - b > 1) {
+        const uint32_t mine = tid[s];
+        for (uint32_t t = b; t < e; ++t) d += tid[t] < mine ? 1u : 0u;
+    }
+    if (d >= e) {
+        atomicOr(err, kErrInternal);
+        return;
+    }
+    opos[d] = pos[i];
+    ovel[d] = vel[i];
+    oid[d] = id[i];
+}
+
+template <class T>
+__global__ void k_rank_gather(const uint32_t *__restrict__ kg, const uint32_t *__restrict__ sg,
+                              const uint32_t *__restrict__ srcg, const uint32_t *__restrict__ tidg,
+                              const V4<T> *__restrict__ pg, const V4<T> *__restrict__ vg,
+                              const uint32_t *__restrict__ ig, V4<T> *__restrict__ opg, V4<T> *__restrict__ ovg,
+                              uint32_t *__restrict__ oig, int ng, const uint32_t *__restrict__ kd,
+                              const uint32_t *__restrict__ sd, const uint32_t *__restrict__ srcd,
+                              const uint32_t *__restrict__ tidd, const V4<T> *__restrict__ pd,
+                              const V4<T> *__restrict__ vd, const uint32_t *__restrict__ id_,
+                              V4<T> *__restrict__ opd, V4<T> *__restrict__ ovd, uint32_t *__restrict__ oid, int nd,
+                              int *err)
+{
+    const int s = blockIdx.x * blockDim.x + threadIdx.x;
+    if (s < ng) rank_move<T>((uint32_t)s, kg, sg, srcg, tidg, pg, vg, ig, opg, ovg, oig, (uint32_t)ng, err);
+    else if (s < ng + nd)
+        rank_move<T>((uint32_t)(s - ng), kd, sd, srcd, tidd, pd, vd, id_, opd, ovd, oid, (uint32_t)nd, err);
+}
+
+// Pack component arrays (x.., v.., [w]) into V4 state; id = index (+ frozen bit).
+template <class T, int DIM>
+__global__ void k_pack(const T *__restrict__ x0, const T *__restrict__ x1, const T *__restrict__ x2,
+                       const T *__restrict__ v0, const T *__restrict__ v1, const T *__restrict__ v2,
+                       const T *__restrict__ w, const uint8_t *__restrict__ frozen, int n, V4<T> *__restrict__ pos,
+                       V4<T> *__restrict__ vel, uint32_t *__restrict__ id)
+{
+    const int i = blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= n) return;
+    V4<T> p, v;
+    p.x = x0[i];
+    p.y = DIM > 1 ? x1[i] : T(0);
+    p.z = DIM > 2 ? x2[i] : T(0);
+    p.w = T(0);
+    v.x = v0[i];
+    v.y = DIM > 1 ? v1[i] : T(0);
+    v.z = DIM > 2 ? v2[i] : T(0);
+    v.w = w ? w[i] : T(0);
+    pos[i] = p;
+    vel[i] = v;
+    id[i] = (uint32_t)i | ((frozen && frozen[i]) ? kFrozenBit : 0u);
+}
+
+// Input checks: bit 1 non-finite, bit 2 moving particle outside [lo, hi),
+// bit 4 t_stop <= 0 (dust only).
+template <class T, int DIM>
+__global__ void k_check(Geo<T> G, const V4<T> *__restrict__ pos, const V4<T> *__restrict__ vel,
+                        const uint32_t *__restrict__ id, int n, int is_gas, T hi0, T hi1, T hi2, int *flags)
+{
+    const int i = blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= n) return;
+    const V4<T> p = pos[i], v = vel[i];
+    int f = 0;
+    const T xs[3] = {p.x, p.y, p.z};
+    const T vs[3] = {v.x, v.y, v.z};
+    const T his[3] = {hi0, hi1, hi2};
+    const bool frozen = is_gas && (id[i] & kFrozenBit);
+    for (int k = 0; k < DIM; ++k) {
+        if (!isfinite(xs[k]) || !isfinite(vs[k])) f |= 1;
+        else if (!frozen && (xs[k] < G.lo[k] || xs[k] >= his[k])) f |= 2;
+    }
+    if (!isfinite(v.w)) f |= 1;
+    if (!is_gas && !(v.w > T(0))) f |= 4;
+    if (f) atomicOr(flags, f);
+}
+
+// Field export: what = 0 position, 1 velocity, 2 vel.w, 3 scalar array aux.
+template <class T>
+__global__ void k_unpack(const V4<T> *__restrict__ pos, const V4<T> *__restrict__ vel,
+                         const uint32_t *__restrict__ id, const T *__restrict__ aux, int n, int dim, int what,
+                         int order, T *__restrict__ out)
+{
+    const int s = blockIdx.x * blockDim.x + threadIdx.x;
+    if (s >= n) return;
+    const size_t o = order == TFSPH_ORDER_ORIGINAL ? (size_t)(id[s] & kIdMask) : (size_t)s;
+    if (what == 0 || what == 1) {
+        const V4<T> v = what == 0 ? pos[s] : vel[s];
+        out[o] = v.x;
+        if (dim > 1) out[(size_t)n + o] = v.y;
+        if (dim > 2) out[2 * (size_t)n + o] = v.z;
+    } else if (what == 2) {
+        out[o] = vel[s].w;
+    } else {
+        out[o] = aux[s];
+    }
+}
+
+// New stopping times in id order into the resident (storage-order) state.
+template <class T>
+__global__ void k_set_tstop(V4<T> *__restrict__ vel, const uint32_t *__restrict__ id, const T *__restrict__ ts,
+                            int n, int *err)
+{
+    const int s = blockIdx.x * blockDim.x + threadIdx.x;
+    if (s >= n) return;
+    const T t = ts[id[s] & kIdMask];
+    if (!(t > T(0)) || !isfinite(t)) atomicOr(err, kErrBadTstop);
+    vel[s].w = t;
+}
+
+// Per-block max over moving gas of max(|v|, c).
+template <class T, int DIM>
+__global__ void __launch_bounds__(256)
+k_max_speed(Phys<T> Ph, const V4<T> *__restrict__ vel, const uint32_t *__restrict__ id, int n,
+            T *__restrict__ partial)
+{
+    __shared__ T red[256];
+    T m = T(0);
+    for (int s = blockIdx.x * blockDim.x + threadIdx.x; s < n; s += gridDim.x * blockDim.x) {
+        if (id[s] & kFrozenBit) continue;
+        const V4<T> v = vel[s];
+        T s2 = v.x * v.x;
+        if (DIM > 1) s2 += v.y * v.y;
+        if (DIM > 2) s2 += v.z * v.z;
+        const T sp = sqrt(s2);
+        const T c = Ph.eos == TFSPH_EOS_ADIABATIC ? sqrt(Ph.gamma * Ph.gm1 * v.w) : Ph.cs;
+        m = fmax(m, fmax(sp, c));
+    }
+    red[threadIdx.x] = m;
+    __syncthreads();
+    for (int o = blockDim.x / 2; o > 0; o >>= 1) {
+        if (threadIdx.x < o) red[threadIdx.x] = fmax(red[threadIdx.x], red[threadIdx.x + o]);
+        __syncthreads();
+    }
+    if (threadIdx.x == 0) partial[blockIdx.x] = red[0];
+}
+
+template <class T>
+__global__ void __launch_bounds__(256) k_max_final(const T *__restrict__ partial, int nblk, T *__restrict__ out)
+{
+    __shared__ T red[256];
+    T m = T(0);
+    for (int i = threadIdx.x; i < nblk; i += blockDim.x) m = fmax(m, partial[i]);
+    red[threadIdx.x] = m;
+    __syncthreads();
+    for (int o = blockDim.x / 2; o > 0; o >>= 1) {
+        if (threadIdx.x < o) red[threadIdx.x] = fmax(red[threadIdx.x], red[threadIdx.x + o]);
+        __syncthreads();
+    }
+    if (threadIdx.x == 0) *out = red[0];
+}
+
+inline int grid_for(int64_t n, int threads) { return (int)((n + threads - 1) / threads); }
+
+template <class T>
+cudaError_t keys_t(const LaunchCtx &L, const void *geo, const PhaseBufs &P)
+{
+    if (P.n == 0) return cudaSuccess;
+    const Geo<T> &G = *static_cast<const Geo<T> *>(geo);
+    auto *pos = static_cast<const V4<T> *>(P.pos[P.cur]);
+    const int n = (int)P.n;
+    switch (L.dim) {
+        case 1: k_keys<T, 1><<<grid_for(n, 256), 256, 0, L.stream>>>(G, pos, n, P.key); break;
+        case 2: k_keys<T, 2><<<grid_for(n, 256), 256, 0, L.stream>>>(G, pos, n, P.key); break;
+        default: k_keys<T, 3><<<grid_for(n, 256), 256, 0, L.stream>>>(G, pos, n, P.key); break;
+    }
+    return cudaGetLastError();
+}
+
+template <class T>
+cudaError_t bin_t(const LaunchCtx &L, const void *geo, PhaseBufs &G, PhaseBufs &D, uint32_t *bsum, int64_t nblk)
+{
+    const Geo<T> &Gm = *static_cast<const Geo<T> *>(geo);
+    const int ng = (int)G.n, nd = (int)D.n;
+    const int ntot = ng + nd;
+    const uint32_t ncells = Gm.ncells;
+    if (ntot > 0)
+        k_count<<<grid_for(ntot, 256), 256, 0, L.stream>>>(G.key, ng, G.count, D.key, nd, D.count);
+    dim3 sg((unsigned)nblk, 2);
+    k_scan_reduce<<<sg, kScanThreads, 0, L.stream>>>(G.count, D.count, ncells, bsum, (uint32_t)nblk);
+    k_scan_top<<<2, kScanThreads, 0, L.stream>>>(bsum, (uint32_t)nblk);
+    k_scan_down<<<sg, kScanThreads, 0, L.stream>>>(G.count, D.count, ncells, bsum, (uint32_t)nblk, G.start,
+                                                   D.start, (uint32_t)ng, (uint32_t)nd);
+    if (ntot > 0) {
+        k_scatter<<<grid_for(ntot, 256), 256, 0, L.stream>>>(G.key, G.id[G.cur], G.count, G.start, G.tmp_src,
+                                                             G.tmp_id, ng, D.key, D.id[D.cur], D.count, D.start,
+                                                             D.tmp_src, D.tmp_id, nd, L.d_err);
+        const int og = G.cur ^ 1, od = D.cur ^ 1;
+        k_rank_gather<T><<<grid_for(ntot, 256), 256, 0, L.stream>>>(
+            G.key, G.start, G.tmp_src, G.tmp_id, static_cast<const V4<T> *>(G.pos[G.cur]),
+            static_cast<const V4<T> *>(G.vel[G.cur]), G.id[G.cur], static_cast<V4<T> *>(G.pos[og]),
+            static_cast<V4<T> *>(G.vel[og]), G.id[og], ng, D.key, D.start, D.tmp_src, D.tmp_id,
+            static_cast<const V4<T> *>(D.pos[D.cur]), static_cast<const V4<T> *>(D.vel[D.cur]), D.id[D.cur],
+            static_cast<V4<T> *>(D.pos[od]), static_cast<V4<T> *>(D.vel[od]), D.id[od], nd, L.d_err);
+        G.cur = og;
+        D.cur = od;
+    }
+    return cudaGetLastError();
+}
+
+template <class T>
+cudaError_t pack_t(const LaunchCtx &L, PhaseBufs &P, const void *const *src, int has_w, const uint8_t *frozen)
+{
+    if (P.n == 0) return cudaSuccess;
+    const int n = (int)P.n;
+    const int d = L.dim;
+    auto c = [&](int k) { return static_cast<const T *>(src[k]); };
+    const T *x0 = c(0), *x1 = d > 1 ? c(1) : nullptr, *x2 = d > 2 ? c(2) : nullptr;
+    const T *v0 = c(d), *v1 = d > 1 ? c(d + 1) : nullptr, *v2 = d > 2 ? c(d + 2) : nullptr;
+    const T *w = has_w ? c(2 * d) : nullptr;
+    auto *pos = static_cast<V4<T> *>(P.pos[P.cur]);
+    auto *vel = static_cast<V4<T> *>(P.vel[P.cur]);
+    switch (d) {
+        case 1: k_pack<T, 1><<<grid_for(n, 256), 256, 0, L.stream>>>(x0, x1, x2, v0, v1, v2, w, frozen, n, pos, vel, P.id[P.cur]); break;
+        case 2: k_pack<T, 2><<<grid_for(n, 256), 256, 0, L.stream>>>(x0, x1, x2, v0, v1, v2, w, frozen, n, pos, vel, P.id[P.cur]); break;
+        default: k_pack<T, 3><<<grid_for(n, 256), 256, 0, L.stream>>>(x0, x1, x2, v0, v1, v2, w, frozen, n, pos, vel, P.id[P.cur]); break;
+    }
+    return cudaGetLastError();
+}
+
+template <class T>
+cudaError_t check_t(const LaunchCtx &L, const void *geo, const PhaseBufs &P, int is_gas, int *flags)
+{
+    if (P.n == 0) return cudaSuccess;
+    const Geo<T> &G = *static_cast<const Geo<T> *>(geo);
+    const int n = (int)P.n;
+    const T hi0 = G.lo[0] + G.L[0], hi1 = G.lo[1] + G.L[1], hi2 = G.lo[2] + G.L[2];
+    auto *pos = static_cast<const V4<T> *>(P.pos[P.cur]);
+    auto *vel = static_cast<const V4<T> *>(P.vel[P.cur]);
+    switch (L.dim) {
+        case 1: k_check<T, 1><<<grid_for(n, 256), 256, 0, L.stream>>>(G, pos, vel, P.id[P.cur], n, is_gas, hi0, hi1, hi2, flags); break;
+        case 2: k_check<T, 2><<<grid_for(n, 256), 256, 0, L.stream>>>(G, pos, vel, P.id[P.cur], n, is_gas, hi0, hi1, hi2, flags); break;
+        default: k_check<T, 3><<<grid_for(n, 256), 256, 0, L.stream>>>(G, pos, vel, P.id[P.cur], n, is_gas, hi0, hi1, hi2, flags); break;
+    }
+    return cudaGetLastError();
+}
+
+template <class T>
+cudaError_t max_speed_t(const LaunchCtx &L, const void *phys, const PhaseBufs &G, void *partials, int nblk,
+                        void *result)
+{
+    const Phys<T> &Ph = *static_cast<const Phys<T> *>(phys);
+    const int n = (int)G.n;
+    auto *vel = static_cast<const V4<T> *>(G.vel[G.cur]);
+    switch (L.dim) {
+        case 1: k_max_speed<T, 1><<<nblk, 256, 0, L.stream>>>(Ph, vel, G.id[G.cur], n, static_cast<T *>(partials)); break;
+        case 2: k_max_speed<T, 2><<<nblk, 256, 0, L.stream>>>(Ph, vel, G.id[G.cur], n, static_cast<T *>(partials)); break;
+        default: k_max_speed<T, 3><<<nblk, 256, 0, L.stream>>>(Ph, vel, G.id[G.cur], n, static_cast<T *>(partials)); break;
+    }
+    k_max_final<T><<<1, 256, 0, L.stream>>>(static_cast<const T *>(partials), nblk, static_cast<T *>(result));
+    return cudaGetLastError();
+}
+
+}  // namespace
+
+cudaError_t launch_keys(const LaunchCtx &L, const void *geo, const PhaseBufs &P)
+{
+    return L.precision == TFSPH_FP64 ? keys_t<double>(L, geo, P) : keys_t<float>(L, geo, P);
+}
+
+cudaError_t launch_bin(const LaunchCtx &L, const void *geo, PhaseBufs &G, PhaseBufs &D, uint32_t *bsum,
+                       int64_t nblk)
+{
+    return L.precision == TFSPH_FP64 ? bin_t<double>(L, geo, G, D, bsum, nblk)
+                                     : bin_t<float>(L, geo, G, D, bsum, nblk);
+}
+
+cudaError_t launch_pack(const LaunchCtx &L, PhaseBufs &P, const void *const *src, int ncomp_v,
+                        const uint8_t *frozen, bool)
+{
+    return L.precision == TFSPH_FP64 ? pack_t<double>(L, P, src, ncomp_v, frozen)
+                                     : pack_t<float>(L, P, src, ncomp_v, frozen);
+}
+
+cudaError_t launch_unpack(const LaunchCtx &L, const PhaseBufs &P, int what, void *out, int order, const void *aux)
+{
+    if (P.n == 0) return cudaSuccess;
+    const int n = (int)P.n;
+    if (L.precision == TFSPH_FP64) {
+        k_unpack<double><<<grid_for(n, 256), 256, 0, L.stream>>>(
+            static_cast<const double4a *>(P.pos[P.cur]), static_cast<const double4a *>(P.vel[P.cur]), P.id[P.cur],
+            static_cast<const double *>(aux), n, L.dim, what, order, static_cast<double *>(out));
+    } else {
+        k_unpack<float><<<grid_for(n, 256), 256, 0, L.stream>>>(
+            static_cast<const float4 *>(P.pos[P.cur]), static_cast<const float4 *>(P.vel[P.cur]), P.id[P.cur],
+            static_cast<const float *>(aux), n, L.dim, what, order, static_cast<float *>(out));
+    }
+    return cudaGetLastError();
+}
+
+cudaError_t launch_set_tstop(const LaunchCtx &L, PhaseBufs &D, const void *t_stop)
+{
+    if (D.n == 0) return cudaSuccess;
+    const int n = (int)D.n;
+    if (L.precision == TFSPH_FP64)
+        k_set_tstop<double><<<grid_for(n, 256), 256, 0, L.stream>>>(static_cast<double4a *>(D.vel[D.cur]),
+                                                                    D.id[D.cur], static_cast<const double *>(t_stop),
+                                                                    n, L.d_err);
+    else
+        k_set_tstop<float><<<grid_for(n, 256), 256, 0, L.stream>>>(static_cast<float4 *>(D.vel[D.cur]), D.id[D.cur],
+                                                                   static_cast<const float *>(t_stop), n, L.d_err);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_check(const LaunchCtx &L, const void *geo, const PhaseBufs &P, int is_gas, int *flags)
+{
+    return L.precision == TFSPH_FP64 ? check_t<double>(L, geo, P, is_gas, flags)
+                                     : check_t<float>(L, geo, P, is_gas, flags);
+}
+
+cudaError_t launch_max_speed(const LaunchCtx &L, const void *phys, const PhaseBufs &G, void *partials, int nblk,
+                             void *result)
+{
+    return L.precision == TFSPH_FP64 ? max_speed_t<double>(L, phys, G, partials, nblk, result)
+                                     : max_speed_t<float>(L, phys, G, partials, nblk, result);
+}
+
+cudaError_t launch_debug_keys(const LaunchCtx &L, const void *geo, const PhaseBufs &P, uint32_t *out)
+{
+    PhaseBufs Q = P;
+    Q.key = out;
+    return launch_keys(L, geo, Q);
+}
+
+}  // namespace tfsph

@@ -1,0 +1,661 @@
+// C ABI of libtfsph: context set-up, the step sequence, field export.
+//
+// Step sequence on the context's stream (no host synchronisation):
+//   [bin]     count -> scan (3 launches) -> scatter -> rank+gather   (bin.cu)
+//   [density] gas summation density and p/rho^2                       (sph.cu)
+//   [force]   gas pressure (+ viscous) acceleration, de/dt             (sph.cu)
+//   [drag]    per-cell implicit drag, particle update, next keys       (drag.cu)
+// The first two form "prepare" and are skipped when a field export has
+// already binned the current positions.
+#include <cstdio>
+#include <cstdlib>
+#include <cstring>
+#include <new>
+#include <string>
+#include <vector>
+
+#include "tfsph_internal.cuh"
+
+using namespace tfsph;
+
+struct tfsph_ctx {
+    tfsph_params p{};
+    int precision = TFSPH_FP32;
+    int dim = 1;
+    int cell_acc = TFSPH_CELL_ACC_FP64;
+    size_t tsize = 4;
+    cudaStream_t stream = nullptr;
+    int device = 0;
+    int ncell[3] = {1, 1, 1};
+    int reach[3] = {0, 0, 0};
+    uint32_t ncells = 1;
+    PhaseBufs G, D;
+    void *rho_g = nullptr;
+    void *rho_d = nullptr;
+    void *acc = nullptr;
+    uint32_t *bsum = nullptr;
+    int64_t nblk = 1;
+    void *partials = nullptr;
+    int npart = 1;
+    void *scalar = nullptr;
+    int *d_err = nullptr;
+    int *d_flags = nullptr;
+    void *staging = nullptr;
+    size_t staging_bytes = 0;
+    alignas(64) unsigned char geo[sizeof(Geo<double>)];
+    alignas(64) unsigned char phys[sizeof(Phys<double>)];
+    bool prepared = false;
+    bool counts_dirty = false;  // a binning did not finish: zero the cell counts first
+    bool has_frozen = false;
+    int64_t steps = 0;
+    int64_t device_bytes = 0;
+    std::vector<void *> allocs;
+    std::string err;
+};
+
+namespace {
+
+thread_local std::string g_init_error;
+
+int fail(tfsph_ctx *c, int code, const std::string &msg)
+{
+    if (c) c->err = msg;
+    else g_init_error = msg;
+    return code;
+}
+
+int cuda_fail(tfsph_ctx *c, cudaError_t e, const char *where)
+{
+    std::string m = std::string(where) + ": " + cudaGetErrorName(e) + " (" + cudaGetErrorString(e) + ")";
+    return fail(c, e == cudaErrorMemoryAllocation ? TFSPH_E_OOM : TFSPH_E_CUDA, m);
+}
+
+#define TF_CUDA(c, call)                                        \
+    do {                                                        \
+        cudaError_t e_ = (call);                                \
+        if (e_ != cudaSuccess) return cuda_fail((c), e_, #call); \
+    } while (0)
+
+int dalloc(tfsph_ctx *c, void **out, size_t bytes)
+{
+    *out = nullptr;
+    if (bytes == 0) bytes = 16;
+    cudaError_t e = cudaMalloc(out, bytes);
+    if (e != cudaSuccess) {
+        *out = nullptr;
+        return cuda_fail(c, e, "cudaMalloc");
+    }
+    c->allocs.push_back(*out);
+    c->device_bytes += (int64_t)bytes;
+    return TFSPH_OK;
+}
+
+template <class T> void build_geo(tfsph_ctx *c)
+{
+    const tfsph_params &p = c->p;
+    Geo<T> G{};
+    G.dim = p.dim;
+    const double u = sizeof(T) == 4 ? 0x1p-24 : 0x1p-53;
+    double span = 0.0;
+    for (int d = 0; d < p.dim; ++d) span = fmax(span, fmax(fabs(p.lo[d]), fabs(p.hi[d])) + (p.hi[d] - p.lo[d]));
+    const double margin = 8.0 * u * span + 16.0 * u * 2.0 * p.h;
+    const double reach = 2.0 * p.h + margin;
+    for (int d = 0; d < 3; ++d) {
+        if (d >= p.dim) {
+            G.n[d] = 1;
+            G.R[d] = 0;
+            G.per[d] = 0;
+            G.full[d] = 0;
+            G.lo[d] = T(0);
+            G.inv_w[d] = T(0);
+            G.w[d] = T(1);
+            G.L[d] = T(1);
+            G.halfL[d] = T(0.5);
+            continue;
+        }
+        const double L = p.hi[d] - p.lo[d];
+        const int n = c->ncell[d];
+        const double w = L / (double)n;
+        G.n[d] = n;
+        G.R[d] = (int)floor(reach / w) + 1;
+        G.per[d] = p.periodic[d] ? 1 : 0;
+        G.full[d] = (G.per[d] && 2 * G.R[d] + 1 >= n) ? 1 : 0;
+        G.lo[d] = T(p.lo[d]);
+        G.inv_w[d] = T((double)n / L);
+        G.w[d] = T(w);
+        G.L[d] = T(L);
+        G.halfL[d] = T(0.5 * L);
+        c->reach[d] = G.R[d];
+    }
+    G.h2x4 = T(4.0 * p.h * p.h);
+    G.lim2 = T(reach * reach * (1.0 + 16.0 * u));
+    const double sigma = p.dim == 1 ? 2.0 / 3.0 : (p.dim == 2 ? 10.0 / (7.0 * M_PI) : 1.0 / M_PI);
+    G.wnorm = T(sigma / pow(p.h, p.dim));
+    G.fnorm = T(sigma / pow(p.h, p.dim + 2));
+    G.inv_h = T(1.0 / p.h);
+    G.h = T(p.h);
+    G.ncells = c->ncells;
+    memcpy(c->geo, &G, sizeof(G));
+
+    Phys<T> Ph{};
+    Ph.m_g = T(p.m_gas);
+    Ph.m_d = T(p.m_dust);
+    Ph.cs = T(p.cs);
+    Ph.cs2 = T(p.cs * p.cs);
+    Ph.gm1 = T(p.gamma - 1.0);
+    Ph.gamma = T(p.gamma);
+    Ph.av_alpha = T(p.av_alpha);
+    Ph.av_beta = T(p.av_beta);
+    Ph.eta2 = T(0.01 * p.h * p.h);
+    Ph.h = T(p.h);
+    Ph.eos = p.eos;
+    Ph.av = (p.av_alpha > 0.0 || p.av_beta > 0.0) ? 1 : 0;
+    memcpy(c->phys, &Ph, sizeof(Ph));
+}
+
+LaunchCtx lctx(const tfsph_ctx *c)
+{
+    LaunchCtx L;
+    L.stream = c->stream;
+    L.precision = c->precision;
+    L.dim = c->dim;
+    L.d_err = c->d_err;
+    return L;
+}
+
+int validate_params(const tfsph_params *p, int64_t ng, int64_t nd, std::string &why)
+{
+    char buf[256];
+    if (!p) { why = "params is NULL"; return TFSPH_E_INVALID_ARG; }
+    if (p->dim < 1 || p->dim > 3) { why = "dim must be 1, 2 or 3"; return TFSPH_E_INVALID_ARG; }
+    if (p->precision != TFSPH_FP32 && p->precision != TFSPH_FP64) { why = "unknown precision"; return TFSPH_E_INVALID_ARG; }
+    if (p->kernel != TFSPH_KERNEL_CUBIC) { why = "unknown kernel"; return TFSPH_E_INVALID_ARG; }
+    if (p->eos != TFSPH_EOS_ISOTHERMAL && p->eos != TFSPH_EOS_ADIABATIC) { why = "unknown eos"; return TFSPH_E_INVALID_ARG; }
+    if (p->tstar_mode != TFSPH_TSTAR_ARITHMETIC && p->tstar_mode != TFSPH_TSTAR_HARMONIC) { why = "unknown tstar_mode"; return TFSPH_E_INVALID_ARG; }
+    if (p->cell_acc != TFSPH_CELL_ACC_FP32 && p->cell_acc != TFSPH_CELL_ACC_FP64) { why = "unknown cell_acc"; return TFSPH_E_INVALID_ARG; }
+    if (p->reserved != 0) { why = "reserved must be 0"; return TFSPH_E_INVALID_ARG; }
+    const double vals[] = {p->h, p->cell_size, p->m_gas, p->m_dust, p->cs, p->gamma, p->av_alpha, p->av_beta};
+    for (double v : vals)
+        if (!std::isfinite(v)) { why = "non-finite parameter"; return TFSPH_E_NONFINITE; }
+    if (!(p->h > 0) || !(p->cell_size > 0)) { why = "h and cell_size must be > 0"; return TFSPH_E_INVALID_ARG; }
+    if (!(p->m_gas > 0) || !(p->m_dust > 0)) { why = "particle masses must be > 0"; return TFSPH_E_INVALID_ARG; }
+    if (!(p->cs > 0)) { why = "cs must be > 0"; return TFSPH_E_INVALID_ARG; }
+    if (p->eos == TFSPH_EOS_ADIABATIC && !(p->gamma > 1.0)) { why = "gamma must be > 1"; return TFSPH_E_INVALID_ARG; }
+    if (p->av_alpha < 0 || p->av_beta < 0) { why = "viscosity coefficients must be >= 0"; return TFSPH_E_INVALID_ARG; }
+    if (ng < 0 || nd < 0 || ng >= (int64_t)1 << 31 || nd >= (int64_t)1 << 31) { why = "particle counts must be in [0, 2^31)"; return TFSPH_E_INVALID_ARG; }
+    double ncells = 1.0;
+    for (int d = 0; d < p->dim; ++d) {
+        if (!std::isfinite(p->lo[d]) || !std::isfinite(p->hi[d])) { why = "non-finite box"; return TFSPH_E_NONFINITE; }
+        const double L = p->hi[d] - p->lo[d];
+        if (!(L > 0)) { why = "box must have hi > lo"; return TFSPH_E_INVALID_ARG; }
+        if (p->periodic[d] && L < 4.0 * p->h) {
+            snprintf(buf, sizeof buf, "periodic axis %d is shorter than 4h (%g < %g)", d, L, 4.0 * p->h);
+            why = buf;
+            return TFSPH_E_INVALID_ARG;
+        }
+        ncells *= fmax(1.0, floor(L / p->cell_size));
+    }
+    if (ncells > 1.0e9) { why = "too many cells (> 1e9); increase cell_size"; return TFSPH_E_INVALID_ARG; }
+    return TFSPH_OK;
+}
+
+// Device copies of user arrays: returns device pointers (host input is staged).
+int stage_inputs(tfsph_ctx *c, const void *const *arrs, int narr, int64_t n, const uint8_t *frozen, int mem_kind,
+                 std::vector<const void *> &dev, const uint8_t **dev_frozen)
+{
+    dev.assign(narr, nullptr);
+    *dev_frozen = nullptr;
+    if (n == 0) return TFSPH_OK;
+    for (int k = 0; k < narr; ++k)
+        if (!arrs[k]) return fail(c, TFSPH_E_INVALID_ARG, "NULL input array");
+    if (mem_kind == TFSPH_MEM_DEVICE) {
+        for (int k = 0; k < narr; ++k) dev[k] = arrs[k];
+        *dev_frozen = frozen;
+        return TFSPH_OK;
+    }
+    const size_t need = (size_t)narr * (size_t)n * c->tsize + (frozen ? (size_t)n + 256 : 0);
+    if (need > c->staging_bytes) return fail(c, TFSPH_E_INTERNAL, "staging buffer too small");
+    char *base = static_cast<char *>(c->staging);
+    for (int k = 0; k < narr; ++k) {
+        char *dst = base + (size_t)k * (size_t)n * c->tsize;
+        TF_CUDA(c, cudaMemcpyAsync(dst, arrs[k], (size_t)n * c->tsize, cudaMemcpyHostToDevice, c->stream));
+        dev[k] = dst;
+    }
+    if (frozen) {
+        char *dst = base + (size_t)narr * (size_t)n * c->tsize;
+        TF_CUDA(c, cudaMemcpyAsync(dst, frozen, (size_t)n, cudaMemcpyHostToDevice, c->stream));
+        *dev_frozen = reinterpret_cast<const uint8_t *>(dst);
+    }
+    return TFSPH_OK;
+}
+
+// Loads a full particle state, computes keys and checks it (synchronises).
+int load_state(tfsph_ctx *c, const void *const *gas, const void *const *dust, const uint8_t *frozen, int mem_kind)
+{
+    if (mem_kind != TFSPH_MEM_HOST && mem_kind != TFSPH_MEM_DEVICE) return fail(c, TFSPH_E_INVALID_ARG, "bad mem_kind");
+    if ((c->G.n > 0 && !gas) || (c->D.n > 0 && !dust)) return fail(c, TFSPH_E_INVALID_ARG, "NULL array list");
+    const int d = c->dim;
+    const int ngas_arr = 2 * d + (c->p.eos == TFSPH_EOS_ADIABATIC ? 1 : 0);
+    const int ndust_arr = 2 * d + 1;
+    LaunchCtx L = lctx(c);
+    std::vector<const void *> dv;
+    const uint8_t *dfz = nullptr;
+    int rc = stage_inputs(c, gas, ngas_arr, c->G.n, frozen, mem_kind, dv, &dfz);
+    if (rc) return rc;
+    c->G.cur = 0;
+    TF_CUDA(c, launch_pack(L, c->G, dv.data(), c->p.eos == TFSPH_EOS_ADIABATIC, dfz, true));
+    // the gas staging area is reused for dust only after the pack has consumed it
+    if (mem_kind == TFSPH_MEM_HOST) TF_CUDA(c, cudaStreamSynchronize(c->stream));
+    rc = stage_inputs(c, dust, ndust_arr, c->D.n, nullptr, mem_kind, dv, &dfz);
+    if (rc) return rc;
+    c->D.cur = 0;
+    TF_CUDA(c, launch_pack(L, c->D, dv.data(), 1, nullptr, false));
+    TF_CUDA(c, launch_keys(L, c->geo, c->G));
+    TF_CUDA(c, launch_keys(L, c->geo, c->D));
+    TF_CUDA(c, cudaMemsetAsync(c->d_flags, 0, sizeof(int), c->stream));
+    TF_CUDA(c, launch_check(L, c->geo, c->G, 1, c->d_flags));
+    TF_CUDA(c, launch_check(L, c->geo, c->D, 0, c->d_flags));
+    int flags = 0;
+    TF_CUDA(c, cudaMemcpyAsync(&flags, c->d_flags, sizeof(int), cudaMemcpyDeviceToHost, c->stream));
+    TF_CUDA(c, cudaStreamSynchronize(c->stream));
+    if (flags & 1) return fail(c, TFSPH_E_NONFINITE, "non-finite position, velocity or energy in the input");
+    if (flags & 4) return fail(c, TFSPH_E_NONFINITE, "dust t_stop must be finite and > 0");
+    if (flags & 2) return fail(c, TFSPH_E_OUT_OF_DOMAIN, "a moving particle lies outside [lo, hi)");
+    bool any_frozen = false;
+    if (frozen && c->G.n > 0) {
+        if (mem_kind == TFSPH_MEM_HOST) {
+            const uint8_t *f = frozen;
+            for (int64_t i = 0; i < c->G.n && !any_frozen; ++i) any_frozen = f[i] != 0;
+        } else {
+            any_frozen = true;  // device flags: assume present (only costs an id read per particle)
+        }
+    }
+    c->has_frozen = any_frozen;
+    c->prepared = false;
+    c->steps = 0;
+    return TFSPH_OK;
+}
+
+int prepare(tfsph_ctx *c)
+{
+    if (c->prepared) return TFSPH_OK;
+    LaunchCtx L = lctx(c);
+    if (c->counts_dirty) {
+        TF_CUDA(c, cudaMemsetAsync(c->G.count, 0, (size_t)c->ncells * 4, c->stream));
+        TF_CUDA(c, cudaMemsetAsync(c->D.count, 0, (size_t)c->ncells * 4, c->stream));
+    }
+    c->counts_dirty = true;
+    TF_CUDA(c, launch_bin(L, c->geo, c->G, c->D, c->bsum, c->nblk));
+    c->counts_dirty = false;
+    TF_CUDA(c, launch_density(L, c->geo, c->phys, c->G, c->rho_g, true, nullptr, nullptr));
+    c->prepared = true;
+    return TFSPH_OK;
+}
+
+__global__ void k_mask_ids(const uint32_t *__restrict__ id, int n, uint32_t *__restrict__ out)
+{
+    const int i = blockIdx.x * blockDim.x + threadIdx.x;
+    if (i < n) out[i] = id[i] & kIdMask;
+}
+
+// Copies `bytes` from device `src` to `out` (host or device), synchronising for host.
+int emit(tfsph_ctx *c, const void *src, size_t bytes, void *out, int mem_kind)
+{
+    if (bytes == 0) return TFSPH_OK;
+    if (mem_kind == TFSPH_MEM_DEVICE) {
+        if (src != out) TF_CUDA(c, cudaMemcpyAsync(out, src, bytes, cudaMemcpyDeviceToDevice, c->stream));
+        return TFSPH_OK;
+    }
+    TF_CUDA(c, cudaMemcpyAsync(out, src, bytes, cudaMemcpyDeviceToHost, c->stream));
+    TF_CUDA(c, cudaStreamSynchronize(c->stream));
+    return TFSPH_OK;
+}
+
+}  // namespace
+
+extern "C" {
+
+int tfsph_version(void) { return 10000; }
+
+const char *tfsph_status_string(int code)
+{
+    switch (code) {
+        case TFSPH_OK: return "TFSPH_OK";
+        case TFSPH_E_INVALID_ARG: return "TFSPH_E_INVALID_ARG";
+        case TFSPH_E_NONFINITE: return "TFSPH_E_NONFINITE";
+        case TFSPH_E_OUT_OF_DOMAIN: return "TFSPH_E_OUT_OF_DOMAIN";
+        case TFSPH_E_CUDA: return "TFSPH_E_CUDA";
+        case TFSPH_E_OOM: return "TFSPH_E_OOM";
+        case TFSPH_E_INTERNAL: return "TFSPH_E_INTERNAL";
+        default: return "TFSPH_E_UNKNOWN";
+    }
+}
+
+const char *tfsph_last_error(const tfsph_ctx *c) { return c ? c->err.c_str() : g_init_error.c_str(); }
+
+void tfsph_destroy(tfsph_ctx *c)
+{
+    if (!c) return;
+    for (void *p : c->allocs) cudaFree(p);
+    delete c;
+}
+
+int tfsph_init(tfsph_ctx **out, const tfsph_params *p, const void *const *gas, int64_t n_gas,
+               const void *const *dust, int64_t n_dust, const uint8_t *frozen, int mem_kind)
+{
+    if (!out) return fail(nullptr, TFSPH_E_INVALID_ARG, "out is NULL");
+    *out = nullptr;
+    std::string why;
+    int rc = validate_params(p, n_gas, n_dust, why);
+    if (rc) return fail(nullptr, rc, why);
+    if (mem_kind != TFSPH_MEM_HOST && mem_kind != TFSPH_MEM_DEVICE) return fail(nullptr, TFSPH_E_INVALID_ARG, "bad mem_kind");
+    if ((n_gas > 0 && !gas) || (n_dust > 0 && !dust)) return fail(nullptr, TFSPH_E_INVALID_ARG, "NULL array list");
+
+    tfsph_ctx *c = new (std::nothrow) tfsph_ctx();
+    if (!c) return fail(nullptr, TFSPH_E_OOM, "host allocation failed");
+    c->p = *p;
+    c->precision = p->precision;
+    c->dim = p->dim;
+    c->cell_acc = p->precision == TFSPH_FP64 ? TFSPH_CELL_ACC_FP64 : p->cell_acc;
+    c->tsize = p->precision == TFSPH_FP64 ? 8 : 4;
+    uint64_t nc = 1;
+    for (int d = 0; d < 3; ++d) {
+        if (d < p->dim) c->ncell[d] = (int)fmax(1.0, floor((p->hi[d] - p->lo[d]) / p->cell_size));
+        else c->ncell[d] = 1;
+        nc *= (uint64_t)c->ncell[d];
+    }
+    c->ncells = (uint32_t)nc;
+    c->G.n = n_gas;
+    c->D.n = n_dust;
+    if (p->precision == TFSPH_FP64) build_geo<double>(c);
+    else build_geo<float>(c);
+
+    auto bail = [&](int code) {
+        std::string m = c->err;
+        tfsph_destroy(c);
+        g_init_error = m;
+        return code;
+    };
+    cudaError_t e = cudaGetDevice(&c->device);
+    if (e != cudaSuccess) return bail(cuda_fail(c, e, "cudaGetDevice"));
+
+    const size_t v4 = 4 * c->tsize;
+    PhaseBufs *ph[2] = {&c->G, &c->D};
+    for (PhaseBufs *P : ph) {
+        const size_t n = (size_t)P->n;
+        void *tmp;
+        for (int b = 0; b < 2; ++b) {
+            if ((rc = dalloc(c, &P->pos[b], n * v4))) return bail(rc);
+            if ((rc = dalloc(c, &P->vel[b], n * v4))) return bail(rc);
+            if ((rc = dalloc(c, &tmp, n * 4))) return bail(rc);
+            P->id[b] = static_cast<uint32_t *>(tmp);
+        }
+        if ((rc = dalloc(c, &tmp, n * 4))) return bail(rc);
+        P->key = static_cast<uint32_t *>(tmp);
+        if ((rc = dalloc(c, &tmp, n * 4))) return bail(rc);
+        P->tmp_src = static_cast<uint32_t *>(tmp);
+        if ((rc = dalloc(c, &tmp, n * 4))) return bail(rc);
+        P->tmp_id = static_cast<uint32_t *>(tmp);
+        if ((rc = dalloc(c, &tmp, (size_t)c->ncells * 4))) return bail(rc);
+        P->count = static_cast<uint32_t *>(tmp);
+        if ((rc = dalloc(c, &tmp, ((size_t)c->ncells + 1) * 4))) return bail(rc);
+        P->start = static_cast<uint32_t *>(tmp);
+        e = cudaMemset(P->count, 0, (size_t)c->ncells * 4);
+        if (e != cudaSuccess) return bail(cuda_fail(c, e, "cudaMemset"));
+    }
+    if ((rc = dalloc(c, &c->rho_g, (size_t)n_gas * c->tsize))) return bail(rc);
+    if ((rc = dalloc(c, &c->rho_d, (size_t)n_dust * c->tsize))) return bail(rc);
+    if ((rc = dalloc(c, &c->acc, (size_t)n_gas * v4))) return bail(rc);
+    c->nblk = ((int64_t)c->ncells + kScanTile - 1) / kScanTile;
+    void *tmp;
+    if ((rc = dalloc(c, &tmp, (size_t)c->nblk * 2 * 4))) return bail(rc);
+    c->bsum = static_cast<uint32_t *>(tmp);
+    c->npart = (int)std::min<int64_t>(1024, std::max<int64_t>(1, (n_gas + 255) / 256));
+    if ((rc = dalloc(c, &c->partials, (size_t)c->npart * c->tsize))) return bail(rc);
+    if ((rc = dalloc(c, &c->scalar, 64))) return bail(rc);
+    if ((rc = dalloc(c, &tmp, 64))) return bail(rc);
+    c->d_err = static_cast<int *>(tmp);
+    if ((rc = dalloc(c, &tmp, 64))) return bail(rc);
+    c->d_flags = static_cast<int *>(tmp);
+    e = cudaMemset(c->d_err, 0, 64);
+    if (e != cudaSuccess) return bail(cuda_fail(c, e, "cudaMemset"));
+    // staging for host I/O: the larger phase's input arrays (+ frozen flags), or a field export
+    const int64_t nmax = std::max<int64_t>(n_gas, n_dust);
+    const size_t stage = std::max<size_t>((size_t)(2 * p->dim + 1) * (size_t)nmax * c->tsize + (size_t)n_gas + 256,
+                                          ((size_t)c->ncells + 1) * 4 + 256);
+    if ((rc = dalloc(c, &c->staging, std::max<size_t>(stage, (size_t)nmax * 8 + 256)))) return bail(rc);
+    c->staging_bytes = std::max<size_t>(stage, (size_t)nmax * 8 + 256);
+
+    rc = load_state(c, gas, dust, frozen, mem_kind);
+    if (rc) return bail(rc);
+    *out = c;
+    return TFSPH_OK;
+}
+
+int tfsph_set_state(tfsph_ctx *c, const void *const *gas, const void *const *dust, const uint8_t *frozen,
+                    int mem_kind)
+{
+    if (!c) return fail(nullptr, TFSPH_E_INVALID_ARG, "ctx is NULL");
+    return load_state(c, gas, dust, frozen, mem_kind);
+}
+
+int tfsph_set_stream(tfsph_ctx *c, void *stream)
+{
+    if (!c) return fail(nullptr, TFSPH_E_INVALID_ARG, "ctx is NULL");
+    c->stream = static_cast<cudaStream_t>(stream);
+    return TFSPH_OK;
+}
+
+int tfsph_step(tfsph_ctx *c, double tau, const void *t_stop, int mem_kind, const double g[3])
+{
+    if (!c) return fail(nullptr, TFSPH_E_INVALID_ARG, "ctx is NULL");
+    if (!std::isfinite(tau) || !(tau > 0)) return fail(c, TFSPH_E_INVALID_ARG, "tau must be finite and > 0");
+    double gg[3] = {0, 0, 0};
+    if (g) {
+        for (int k = 0; k < 3; ++k) {
+            if (!std::isfinite(g[k])) return fail(c, TFSPH_E_NONFINITE, "non-finite gravity");
+            gg[k] = k < c->dim ? g[k] : 0.0;
+        }
+    }
+    LaunchCtx L = lctx(c);
+    if (t_stop && c->D.n > 0) {
+        if (mem_kind == TFSPH_MEM_HOST) {
+            const size_t bytes = (size_t)c->D.n * c->tsize;
+            if (c->precision == TFSPH_FP64) {
+                const double *t = static_cast<const double *>(t_stop);
+                for (int64_t j = 0; j < c->D.n; ++j)
+                    if (!(t[j] > 0) || !std::isfinite(t[j])) return fail(c, TFSPH_E_NONFINITE, "t_stop must be finite and > 0");
+            } else {
+                const float *t = static_cast<const float *>(t_stop);
+                for (int64_t j = 0; j < c->D.n; ++j)
+                    if (!(t[j] > 0) || !std::isfinite(t[j])) return fail(c, TFSPH_E_NONFINITE, "t_stop must be finite and > 0");
+            }
+            TF_CUDA(c, cudaMemcpyAsync(c->staging, t_stop, bytes, cudaMemcpyHostToDevice, c->stream));
+            TF_CUDA(c, launch_set_tstop(L, c->D, c->staging));
+        } else if (mem_kind == TFSPH_MEM_DEVICE) {
+            TF_CUDA(c, launch_set_tstop(L, c->D, t_stop));
+        } else {
+            return fail(c, TFSPH_E_INVALID_ARG, "bad mem_kind");
+        }
+    }
+    int rc = prepare(c);
+    if (rc) return rc;
+    if (c->G.n > 0) TF_CUDA(c, launch_force(L, c->geo, c->phys, c->G, c->rho_g, c->acc));
+    StepArgs S;
+    S.tau = tau;
+    S.g[0] = gg[0];
+    S.g[1] = gg[1];
+    S.g[2] = gg[2];
+    S.tstar_mode = c->p.tstar_mode;
+    S.cell_acc = c->cell_acc;
+    S.has_frozen = c->has_frozen ? 1 : 0;
+    TF_CUDA(c, launch_cell_update(L, c->geo, c->phys, c->G, c->D, c->acc, S));
+    c->prepared = false;
+    c->steps += 1;
+    return TFSPH_OK;
+}
+
+int tfsph_max_dt(tfsph_ctx *c, double cfl, double *tau_out)
+{
+    if (!c || !tau_out) return fail(c, TFSPH_E_INVALID_ARG, "NULL argument");
+    if (!(cfl > 0) || !std::isfinite(cfl)) return fail(c, TFSPH_E_INVALID_ARG, "cfl must be finite and > 0");
+    double vmax = c->p.cs;
+    if (c->G.n > 0) {
+        LaunchCtx L = lctx(c);
+        TF_CUDA(c, launch_max_speed(L, c->phys, c->G, c->partials, c->npart, c->scalar));
+        if (c->precision == TFSPH_FP64) {
+            TF_CUDA(c, cudaMemcpyAsync(&vmax, c->scalar, 8, cudaMemcpyDeviceToHost, c->stream));
+            TF_CUDA(c, cudaStreamSynchronize(c->stream));
+        } else {
+            float v = 0;
+            TF_CUDA(c, cudaMemcpyAsync(&v, c->scalar, 4, cudaMemcpyDeviceToHost, c->stream));
+            TF_CUDA(c, cudaStreamSynchronize(c->stream));
+            vmax = v;
+        }
+    }
+    if (!(vmax > 0)) return fail(c, TFSPH_E_INTERNAL, "no moving gas particle with a nonzero signal speed");
+    *tau_out = cfl * c->p.h / vmax;
+    return TFSPH_OK;
+}
+
+int tfsph_fields(tfsph_ctx *c, int field, void *out, int mem_kind, int order)
+{
+    if (!c) return fail(nullptr, TFSPH_E_INVALID_ARG, "ctx is NULL");
+    if (order != TFSPH_ORDER_ORIGINAL && order != TFSPH_ORDER_CELL) return fail(c, TFSPH_E_INVALID_ARG, "bad order");
+    if (mem_kind != TFSPH_MEM_HOST && mem_kind != TFSPH_MEM_DEVICE) return fail(c, TFSPH_E_INVALID_ARG, "bad mem_kind");
+    const PhaseBufs *P;
+    int what, ncomp;
+    const void *aux = nullptr;
+    LaunchCtx L = lctx(c);
+    int rc;
+    switch (field) {
+        case TFSPH_FIELD_POS_G: P = &c->G; what = 0; ncomp = c->dim; break;
+        case TFSPH_FIELD_VEL_G: P = &c->G; what = 1; ncomp = c->dim; break;
+        case TFSPH_FIELD_ENERGY_G: P = &c->G; what = 2; ncomp = 1; break;
+        case TFSPH_FIELD_RHO_G:
+            if ((rc = prepare(c))) return rc;
+            P = &c->G; what = 3; ncomp = 1; aux = c->rho_g;
+            break;
+        case TFSPH_FIELD_POS_D: P = &c->D; what = 0; ncomp = c->dim; break;
+        case TFSPH_FIELD_VEL_D: P = &c->D; what = 1; ncomp = c->dim; break;
+        case TFSPH_FIELD_TSTOP_D: P = &c->D; what = 2; ncomp = 1; break;
+        case TFSPH_FIELD_RHO_D:
+            if ((rc = prepare(c))) return rc;
+            TF_CUDA(c, launch_density(L, c->geo, c->phys, c->D, c->rho_d, false, nullptr, nullptr));
+            P = &c->D; what = 3; ncomp = 1; aux = c->rho_d;
+            break;
+        default: return fail(c, TFSPH_E_INVALID_ARG, "unknown field");
+    }
+    if (P->n == 0) return TFSPH_OK;
+    if (!out) return fail(c, TFSPH_E_INVALID_ARG, "out is NULL");
+    const size_t bytes = (size_t)ncomp * (size_t)P->n * c->tsize;
+    void *dst = mem_kind == TFSPH_MEM_DEVICE ? out : c->staging;
+    if (mem_kind == TFSPH_MEM_HOST && bytes > c->staging_bytes) return fail(c, TFSPH_E_INTERNAL, "staging too small");
+    TF_CUDA(c, launch_unpack(L, *P, what, dst, order, aux));
+    return emit(c, dst, bytes, out, mem_kind);
+}
+
+int tfsph_debug(tfsph_ctx *c, int what, void *out, int mem_kind)
+{
+    if (!c) return fail(nullptr, TFSPH_E_INVALID_ARG, "ctx is NULL");
+    if (!out) return fail(c, TFSPH_E_INVALID_ARG, "out is NULL");
+    if (mem_kind != TFSPH_MEM_HOST && mem_kind != TFSPH_MEM_DEVICE) return fail(c, TFSPH_E_INVALID_ARG, "bad mem_kind");
+    LaunchCtx L = lctx(c);
+    int rc;
+    if (what == TFSPH_DEBUG_ACC_G) {
+        // storage order of the last step is still current until the next binning
+        if (c->G.n == 0) return TFSPH_OK;
+        PhaseBufs Q = c->G;
+        const size_t bytes = (size_t)c->dim * (size_t)c->G.n * c->tsize;
+        void *dst = mem_kind == TFSPH_MEM_DEVICE ? out : c->staging;
+        // reuse the unpack kernel: acc as "pos" of a phase view
+        Q.pos[Q.cur] = c->acc;
+        TF_CUDA(c, launch_unpack(L, Q, 0, dst, TFSPH_ORDER_ORIGINAL, nullptr));
+        return emit(c, dst, bytes, out, mem_kind);
+    }
+    if ((rc = prepare(c))) return rc;
+    const PhaseBufs &P = (what == TFSPH_DEBUG_KEYS_D || what == TFSPH_DEBUG_PERM_D || what == TFSPH_DEBUG_CSTART_D) ? c->D : c->G;
+    void *dst = mem_kind == TFSPH_MEM_DEVICE ? out : c->staging;
+    size_t bytes = 0;
+    switch (what) {
+        case TFSPH_DEBUG_KEYS_G:
+        case TFSPH_DEBUG_KEYS_D:
+            if (P.n == 0) return TFSPH_OK;
+            TF_CUDA(c, launch_debug_keys(L, c->geo, P, static_cast<uint32_t *>(dst)));
+            bytes = (size_t)P.n * 4;
+            break;
+        case TFSPH_DEBUG_PERM_G:
+        case TFSPH_DEBUG_PERM_D:
+            if (P.n == 0) return TFSPH_OK;
+            k_mask_ids<<<(unsigned)((P.n + 255) / 256), 256, 0, c->stream>>>(P.id[P.cur], (int)P.n, static_cast<uint32_t *>(dst));
+            TF_CUDA(c, cudaGetLastError());
+            bytes = (size_t)P.n * 4;
+            break;
+        case TFSPH_DEBUG_CSTART_G:
+        case TFSPH_DEBUG_CSTART_D:
+            bytes = ((size_t)c->ncells + 1) * 4;
+            if (mem_kind == TFSPH_MEM_DEVICE) TF_CUDA(c, cudaMemcpyAsync(out, P.start, bytes, cudaMemcpyDeviceToDevice, c->stream));
+            else {
+                TF_CUDA(c, cudaMemcpyAsync(out, P.start, bytes, cudaMemcpyDeviceToHost, c->stream));
+                TF_CUDA(c, cudaStreamSynchronize(c->stream));
+            }
+            return TFSPH_OK;
+        case TFSPH_DEBUG_NEIGH_COUNT:
+        case TFSPH_DEBUG_NEIGH_FPRINT: {
+            if (c->G.n == 0) return TFSPH_OK;
+            const size_t n = (size_t)c->G.n;
+            // counts and fingerprints into staging-sized temporaries
+            void *cnt = nullptr, *fp = nullptr, *rho = nullptr;
+            cudaError_t e = cudaMallocAsync(&cnt, n * 4, c->stream);
+            if (e == cudaSuccess) e = cudaMallocAsync(&fp, n * 8, c->stream);
+            if (e == cudaSuccess) e = cudaMallocAsync(&rho, n * c->tsize, c->stream);
+            if (e == cudaSuccess)
+                e = launch_density(L, c->geo, c->phys, c->G, rho, true, static_cast<int32_t *>(cnt),
+                                   static_cast<uint64_t *>(fp));
+            if (e == cudaSuccess) {
+                const void *src = what == TFSPH_DEBUG_NEIGH_COUNT ? cnt : fp;
+                const size_t b = n * (what == TFSPH_DEBUG_NEIGH_COUNT ? 4 : 8);
+                e = cudaMemcpyAsync(out, src, b, mem_kind == TFSPH_MEM_DEVICE ? cudaMemcpyDeviceToDevice : cudaMemcpyDeviceToHost, c->stream);
+            }
+            if (cnt) cudaFreeAsync(cnt, c->stream);
+            if (fp) cudaFreeAsync(fp, c->stream);
+            if (rho) cudaFreeAsync(rho, c->stream);
+            if (e != cudaSuccess) return cuda_fail(c, e, "neighbour statistics");
+            if (mem_kind == TFSPH_MEM_HOST) TF_CUDA(c, cudaStreamSynchronize(c->stream));
+            return TFSPH_OK;
+        }
+        default: return fail(c, TFSPH_E_INVALID_ARG, "unknown debug export");
+    }
+    return emit(c, dst, bytes, out, mem_kind);
+}
+
+int tfsph_info(const tfsph_ctx *c, tfsph_info_t *out)
+{
+    if (!c || !out) return TFSPH_E_INVALID_ARG;
+    out->n_gas = c->G.n;
+    out->n_dust = c->D.n;
+    for (int d = 0; d < 3; ++d) {
+        out->n_cells[d] = c->ncell[d];
+        out->reach[d] = c->reach[d];
+    }
+    out->n_cells_total = c->ncells;
+    out->steps = c->steps;
+    out->device_bytes = c->device_bytes;
+    return TFSPH_OK;
+}
+
+int tfsph_sync(tfsph_ctx *c)
+{
+    if (!c) return fail(nullptr, TFSPH_E_INVALID_ARG, "ctx is NULL");
+    TF_CUDA(c, cudaStreamSynchronize(c->stream));
+    int err = 0;
+    TF_CUDA(c, cudaMemcpy(&err, c->d_err, sizeof(int), cudaMemcpyDeviceToHost));
+    if (err) {
+        TF_CUDA(c, cudaMemset(c->d_err, 0, sizeof(int)));
+        if (err & kErrBadTstop) return fail(c, TFSPH_E_NONFINITE, "a t_stop value was <= 0 or not finite");
+        return fail(c, TFSPH_E_INTERNAL, "device-side consistency check failed");
+    }
+    return TFSPH_OK;
+}
+
+}  // extern "C"

@@ -1,0 +1,213 @@
+// Internal declarations shared by the CUDA translation units of libtfsph.
+//
+// Data layout in HBM (per phase, structure of arrays, double-buffered for the
+// gather into cell order):
+//   pos[2]  : V4<T> per particle. Gas: (x, y, z, p/rho^2 after the density
+//             pass); dust: (x, y, z, 0).
+//   vel[2]  : V4<T> per particle. Gas: (vx, vy, vz, e); dust: (ux, uy, uz, t_stop).
+//   id[2]   : uint32 particle id; bit 31 marks a frozen (wall) gas particle.
+//   key     : uint32 cell key of the particle in each storage slot, written by
+//             the update of the previous step (or at set-up).
+//   count   : uint32 per cell, zero between steps (the scatter counts it down).
+//   start   : uint32 per cell + 1, first storage slot of each cell.
+// Gas only: rho (T) and acc (V4<T>: ax, ay, az, de/dt).
+#pragma once
+
+#include <cuda_runtime.h>
+
+#include <cmath>
+#include <cstdint>
+
+#include "tfsph.h"
+
+namespace tfsph {
+
+constexpr uint32_t kIdMask = 0x7fffffffu;
+constexpr uint32_t kFrozenBit = 0x80000000u;
+
+// Device error word bits (set by kernels, read by tfsph_sync).
+constexpr int kErrBadTstop = 1;
+constexpr int kErrInternal = 2;
+
+struct alignas(32) double4a {
+    double x, y, z, w;
+};
+
+template <class T> struct Vec4Of;
+template <> struct Vec4Of<float> { using type = float4; };
+template <> struct Vec4Of<double> { using type = double4a; };
+template <class T> using V4 = typename Vec4Of<T>::type;
+
+// IEEE operations with explicit round-to-nearest, so the compiler cannot fuse
+// them; used wherever a floating-point result decides an integer (cell keys,
+// neighbour membership) and must match the checker's plain arithmetic.
+__device__ __forceinline__ float add_rn(float a, float b) { return __fadd_rn(a, b); }
+__device__ __forceinline__ double add_rn(double a, double b) { return __dadd_rn(a, b); }
+__device__ __forceinline__ float sub_rn(float a, float b) { return __fsub_rn(a, b); }
+__device__ __forceinline__ double sub_rn(double a, double b) { return __dsub_rn(a, b); }
+__device__ __forceinline__ float mul_rn(float a, float b) { return __fmul_rn(a, b); }
+__device__ __forceinline__ double mul_rn(double a, double b) { return __dmul_rn(a, b); }
+
+// Grid geometry and neighbour-search constants, built on the host in double
+// and rounded once to T.
+template <class T> struct Geo {
+    int dim;
+    int n[3];      // cells per axis
+    int R[3];      // reach in cells per axis
+    int per[3];    // periodic axis
+    int full[3];   // periodic axis whose window covers every cell
+    T lo[3];
+    T inv_w[3];    // cells per unit length, (T)(n / L)
+    T w[3];        // cell edge
+    T L[3];        // box edge (periodic axes)
+    T halfL[3];
+    T h2x4;        // (T)(4 h^2): neighbour iff r^2 < h2x4
+    T lim2;        // squared pruning radius for candidate cells (2h plus margin)
+    T wnorm;       // sigma_d / h^d
+    T fnorm;       // sigma_d / h^(d+2): (1/r) dW/dr = fnorm * g(q)
+    T inv_h;
+    T h;
+    uint32_t ncells;
+};
+
+template <class T> struct Phys {
+    T m_g, m_d;
+    T cs, cs2;
+    T gm1, gamma;     // gamma - 1, gamma
+    T av_alpha, av_beta;
+    T eta2;           // 0.01 h^2
+    T h;
+    int eos;
+    int av;
+};
+
+struct PhaseBufs {
+    int64_t n = 0;
+    void *pos[2] = {nullptr, nullptr};
+    void *vel[2] = {nullptr, nullptr};
+    uint32_t *id[2] = {nullptr, nullptr};
+    uint32_t *key = nullptr;
+    uint32_t *count = nullptr;
+    uint32_t *start = nullptr;
+    uint32_t *tmp_src = nullptr;
+    uint32_t *tmp_id = nullptr;
+    int cur = 0;
+};
+
+// Scan partials: blocks of kScanTile cells.
+constexpr int kScanThreads = 256;
+constexpr int kScanItems = 8;
+constexpr int kScanTile = kScanThreads * kScanItems;
+
+// Cell-update CTA: one thread per cell in phase 1.
+constexpr int kCellsPerCta = 128;
+
+// ---------------------------------------------------------------------------
+// Launchers (host functions), grouped by translation unit.
+// ---------------------------------------------------------------------------
+struct LaunchCtx {
+    cudaStream_t stream;
+    int precision;   // TFSPH_FP32 / TFSPH_FP64
+    int dim;
+    int *d_err;      // device error word
+};
+
+// bin.cu
+cudaError_t launch_keys(const LaunchCtx &L, const void *geo, const PhaseBufs &P);
+cudaError_t launch_bin(const LaunchCtx &L, const void *geo, PhaseBufs &G, PhaseBufs &D,
+                       uint32_t *bsum, int64_t nblk);
+cudaError_t launch_pack(const LaunchCtx &L, PhaseBufs &P, const void *const *src, int ncomp_v,
+                        const uint8_t *frozen, bool is_gas);
+cudaError_t launch_unpack(const LaunchCtx &L, const PhaseBufs &P, int what, void *out, int order,
+                          const void *aux);
+cudaError_t launch_set_tstop(const LaunchCtx &L, PhaseBufs &D, const void *t_stop);
+cudaError_t launch_check(const LaunchCtx &L, const void *geo, const PhaseBufs &P, int is_gas,
+                         int *flags);
+cudaError_t launch_max_speed(const LaunchCtx &L, const void *phys, const PhaseBufs &G,
+                             void *partials, int nblk, void *result);
+cudaError_t launch_debug_keys(const LaunchCtx &L, const void *geo, const PhaseBufs &P, uint32_t *out);
+
+// sph.cu
+cudaError_t launch_density(const LaunchCtx &L, const void *geo, const void *phys, PhaseBufs &P,
+                           void *rho, bool gas, int32_t *cnt, uint64_t *fprint);
+cudaError_t launch_force(const LaunchCtx &L, const void *geo, const void *phys, PhaseBufs &G,
+                         const void *rho, void *acc);
+
+// drag.cu
+struct StepArgs {
+    double tau;
+    double g[3];
+    int tstar_mode;
+    int cell_acc;
+    int has_frozen;
+};
+cudaError_t launch_cell_update(const LaunchCtx &L, const void *geo, const void *phys,
+                               PhaseBufs &G, PhaseBufs &D, const void *acc, const StepArgs &S);
+
+// ---------------------------------------------------------------------------
+// Device helpers shared by the kernels.
+// ---------------------------------------------------------------------------
+template <class T> __device__ __forceinline__ int axis_cell(T x, T lo, T inv, int n, T &t)
+{
+    t = mul_rn(sub_rn(x, lo), inv);
+    T f = floor(t);
+    int i;
+    if (!(f >= T(0))) i = 0;          // negative or NaN
+    else if (f >= T(n)) i = n - 1;
+    else i = (int)f;
+    return i;
+}
+
+template <class T, int DIM>
+__device__ __forceinline__ uint32_t cell_key(const Geo<T> &G, T x, T y, T z)
+{
+    T t;
+    int ix = axis_cell(x, G.lo[0], G.inv_w[0], G.n[0], t);
+    int iy = DIM > 1 ? axis_cell(y, G.lo[1], G.inv_w[1], G.n[1], t) : 0;
+    int iz = DIM > 2 ? axis_cell(z, G.lo[2], G.inv_w[2], G.n[2], t) : 0;
+    return (uint32_t)ix + (uint32_t)G.n[0] * ((uint32_t)iy + (uint32_t)G.n[1] * (uint32_t)iz);
+}
+
+// Minimum-image displacement along one axis, in the order the checker uses.
+template <class T> __device__ __forceinline__ T min_image(T d, int per, T L, T half)
+{
+    if (per) {
+        if (d > half) d = sub_rn(d, L);
+        else if (d < -half) d = add_rn(d, L);
+    }
+    return d;
+}
+
+// Periodic image of x in [lo, lo + L).
+template <class T> __device__ __forceinline__ T wrap_periodic(T x, T lo, T L)
+{
+    T y = x - lo;
+    y -= L * floor(y / L);
+    T r = lo + y;
+    if (r >= lo + L) r = lo;
+    if (r < lo) r = lo;
+    return r;
+}
+
+// M4 cubic spline (support 2h): W = wnorm * w(q), (1/r) dW/dr = fnorm * f(q).
+template <class T> __device__ __forceinline__ T kernel_w(const Geo<T> &G, T q)
+{
+    if (q < T(1)) return G.wnorm * (T(1) - T(1.5) * q * q + T(0.75) * q * q * q);
+    if (q < T(2)) {
+        T a = T(2) - q;
+        return G.wnorm * T(0.25) * a * a * a;
+    }
+    return T(0);
+}
+
+template <class T> __device__ __forceinline__ T kernel_f(const Geo<T> &G, T q)
+{
+    if (q < T(1)) return G.fnorm * (T(-3) + T(2.25) * q);
+    if (q < T(2)) {
+        T a = T(2) - q;
+        return G.fnorm * (T(-0.75) * a * a / q);
+    }
+    return T(0);
+}
+
+}  // namespace tfsph

@@ -1,0 +1,284 @@
+"""GPU path against the FP64 oracle, element by element, on seeded inputs.
+
+Bit-exact: cell keys, the (cell key, id) sort order, cell ranges, and the
+neighbour sets (count and fingerprint per particle). Within tolerance after
+one step: gas density, pressure acceleration, velocities, positions and
+energy. Tolerances (normwise ||x - x_ref|| / ||x_ref||): 1e-5 for the FP32
+path and 1e-12 for the FP64 path on density and velocities.
+"""
+import math
+
+import numpy as np
+import pytest
+
+import workloads
+from conftest import gpu_context, gpu_lib, gpu_one_step, normwise, oracle_params
+
+pytestmark = pytest.mark.gpu
+
+TOL = {0: 1e-5, 1: 1e-12}
+
+
+def _oracle_step(orc, w, tau=None, g=None, **pover):
+    p = oracle_params(w, **pover)
+    s = orc.make_state(p, w.gx, w.gv, w.dx, w.du, w.tstop, ge=w.ge, frozen=w.frozen)
+    r = orc.step(p, s, w.tau if tau is None else tau, w.g if g is None else g)
+    rho_d, _, _ = orc.density(p, w.dx, p.m_dust)
+    return p, s, r, rho_d
+
+
+def _pos_err(a, ref, w):
+    """Normwise position error with periodic differences taken as minimum images."""
+    d = np.asarray(a) - np.asarray(ref)
+    for k in range(w.dim):
+        if w.params["periodic"][k]:
+            L = w.params["hi"][k] - w.params["lo"][k]
+            d[k] -= L * np.round(d[k] / L)
+    return float(np.linalg.norm(d)) / float(np.linalg.norm(ref))
+
+
+def _compare(orc, w, tol=None, acc_floor=0.0, **over):
+    prec = int(over.get("precision", w.params["precision"]))
+    tol = TOL[prec] if tol is None else tol
+    gpu = gpu_one_step(w, **over)
+    p, s, r, rho_d = _oracle_step(orc, w)
+    # --- bit-exact integer results ---
+    assert np.array_equal(gpu["perm_g"], r.perm_g), "gas sort order"
+    assert np.array_equal(gpu["perm_d"], r.perm_d), "dust sort order"
+    assert np.array_equal(gpu["keys_g"], r.keys_g[r.perm_g]), "gas cell keys"
+    assert np.array_equal(gpu["keys_d"], r.keys_d[r.perm_d]), "dust cell keys"
+    assert np.array_equal(gpu["cstart_g"], r.cstart_g), "gas cell ranges"
+    assert np.array_equal(gpu["cstart_d"], r.cstart_d), "dust cell ranges"
+    assert np.array_equal(gpu["nb_count"], r.nb_count[r.perm_g]), "neighbour counts"
+    assert np.array_equal(gpu["nb_fprint"], r.nb_fprint[r.perm_g]), "neighbour sets"
+    # --- floating point after one step ---
+    errs = {
+        "rho_g": normwise(gpu["rho_g"], r.rho_g),
+        "rho_d": normwise(gpu["rho_d"], rho_d),
+        "acc_g": normwise(gpu["acc_g"], r.acc_g, floor=acc_floor),
+        "gv": normwise(gpu["gv"], s.gv),
+        "du": normwise(gpu["du"], s.du),
+        "gx": _pos_err(gpu["gx"], s.gx, w),
+        "dx": _pos_err(gpu["dx"], s.dx, w),
+    }
+    if w.params["eos"] == 1:
+        errs["ge"] = normwise(gpu["ge"], s.ge)
+    for k, e in errs.items():
+        assert e <= tol, f"{k}: normwise error {e:.3e} > {tol:.0e} ({errs})"
+    return gpu, r, errs
+
+
+# ---------------------------------------------------------------------------
+# Workloads at sizes the oracle finishes in seconds (several tiles, ragged tails)
+# ---------------------------------------------------------------------------
+def test_dustywave_fp64_one_step(orc):
+    _compare(orc, workloads.dustywave(precision=1))
+
+
+def test_dustywave_fp32_one_step(orc):
+    _compare(orc, workloads.dustywave(n=1000, precision=0))
+
+
+@pytest.mark.parametrize("cell_acc", [0, 1])
+def test_dustyshock_fp32_one_step(orc, cell_acc):
+    w = workloads.dustyshock(n_left=4000, n_right=500, precision=0)
+    _compare(orc, w, cell_acc=cell_acc)
+
+
+def test_dustyshock_fp64_one_step(orc):
+    w = workloads.dustyshock(n_left=1600, n_right=200, precision=1)
+    _compare(orc, w)
+
+
+@pytest.mark.parametrize("nside", [12, 23])
+def test_box3d_fp32_one_step(orc, nside):
+    _compare(orc, workloads.box3d(nside=nside, precision=0))
+
+
+def test_box3d_fp64_one_step(orc):
+    _compare(orc, workloads.box3d(nside=10, precision=1))
+
+
+def test_column2d_fp32_one_step(orc):
+    _compare(orc, workloads.column2d(nside=64, precision=0))
+
+
+def test_column2d_fp64_one_step(orc):
+    _compare(orc, workloads.column2d(nside=32, precision=1))
+
+
+def test_harmonic_tstar_fp64(orc):
+    w = workloads.dustyshock(n_left=800, n_right=100, precision=1)
+    w.params["tstar_mode"] = 1
+    _compare(orc, w)
+
+
+# ---------------------------------------------------------------------------
+# Edge cases
+# ---------------------------------------------------------------------------
+def test_no_dust(orc):
+    w = workloads.dustyshock(n_left=800, n_right=100, with_dust=False, precision=1)
+    _compare(orc, w)
+
+
+def test_no_gas(orc):
+    w = workloads.dustywave(n=50, precision=1)
+    w.gx, w.gv = w.gx[:, :0], w.gv[:, :0]
+    gpu = gpu_one_step(w)
+    p, s, r, _ = _oracle_step(orc, w)
+    np.testing.assert_allclose(gpu["du"], s.du, rtol=1e-14, atol=1e-300)
+    assert np.array_equal(gpu["cstart_d"], r.cstart_d)
+
+
+def test_single_particles(orc):
+    w = workloads.dustywave(n=1, precision=1)
+    w.params["h"] = 0.2
+    w.params["cell_size"] = 0.3
+    _compare(orc, w)
+
+
+def test_all_particles_in_one_cell(orc):
+    """A cluster far denser than the rest: large segments in the rank sort."""
+    rng = np.random.default_rng(17)
+    w = workloads.box3d(nside=8, precision=0)
+    w.gx[:, :300] = 0.5 + rng.uniform(0, 0.01, (3, 300))
+    w.dx[:, :200] = 0.5 + rng.uniform(0, 0.01, (3, 200))
+    w.gx = w.gx.astype(np.float32).astype(np.float64)
+    w.dx = w.dx.astype(np.float32).astype(np.float64)
+    _compare(orc, w, tol=2e-5)
+
+
+def test_particles_on_cell_faces(orc):
+    """Positions exactly on cell faces and on the periodic boundary."""
+    w = workloads.box3d(nside=8, precision=0)
+    w.gx[:, ::7] = np.round(w.gx[:, ::7] * 8) / 8
+    w.dx[:, ::5] = np.round(w.dx[:, ::5] * 8) / 8 % 1.0
+    _compare(orc, w)
+
+
+def test_full_periodic_window(orc):
+    """Fewer cells than the search window along every periodic axis."""
+    w = workloads.box3d(nside=6, precision=1, h_factor=1.2, cell_factor=1.0)
+    _compare(orc, w)
+
+
+@pytest.mark.parametrize("tau_over_t", [1e-3, 1.0, 1e3, 1e6])
+def test_stiff_drag_limits(orc, tau_over_t):
+    w = workloads.dustywave(n=200, precision=1)
+    w.tstop[:] = w.tau / tau_over_t
+    _compare(orc, w)
+
+
+# ---------------------------------------------------------------------------
+# Other entry points
+# ---------------------------------------------------------------------------
+@pytest.mark.parametrize("prec", [0, 1])
+def test_max_dt_matches_oracle(orc, prec):
+    w = workloads.dustyshock(n_left=800, n_right=100, precision=prec)
+    p = oracle_params(w)
+    ref = orc.max_dt(p, w.gv, w.ge, w.frozen, cfl=0.3)
+    with gpu_context(w) as c:
+        got = c.max_dt(0.3)
+    assert abs(got - ref) <= (1e-6 if prec == 0 else 1e-14) * ref
+
+
+def test_tstop_argument_replaces_resident_values(orc):
+    b = gpu_lib()
+    w = workloads.dustyshock(n_left=800, n_right=100, precision=1)
+    new_t = np.random.default_rng(3).uniform(1e-4, 1e-2, w.n_dust)
+    w2 = workloads.dustyshock(n_left=800, n_right=100, precision=1)
+    w2.tstop = new_t.copy()
+    with gpu_context(w) as c:
+        c.step(w.tau, w.g, tstop=new_t)
+        gv = c.field(b.TFSPH_FIELD_VEL_G)
+        ts = c.field(b.TFSPH_FIELD_TSTOP_D)
+    _, s, _, _ = _oracle_step(orc, w2)
+    assert np.array_equal(ts, new_t)
+    assert normwise(gv, s.gv) < 1e-12
+
+
+def test_bad_tstop_is_reported(orc):
+    b = gpu_lib()
+    w = workloads.dustywave(n=50, precision=1)
+    with gpu_context(w) as c:
+        bad = np.full(w.n_dust, 1e-3)
+        bad[7] = np.nan
+        with pytest.raises(b.TfsphError) as ei:
+            c.step(w.tau, w.g, tstop=bad)
+        assert ei.value.code == b.TFSPH_E_NONFINITE
+        c.step(w.tau, w.g)  # the context stays usable
+        c.sync()
+
+
+def test_device_inputs_match_host_inputs(orc):
+    torch = pytest.importorskip("torch")
+    b = gpu_lib()
+    w = workloads.box3d(nside=10, precision=0)
+    ref = gpu_one_step(w)
+    p = b.params_from_dict(w.params)
+    t = lambda a: torch.tensor(a, dtype=torch.float32, device="cuda")
+    with b.Context(p, t(w.gx), t(w.gv), t(w.dx), t(w.du), t(w.tstop)) as c:
+        c.set_stream(torch.cuda.current_stream())
+        c.step(w.tau, w.g)
+        out = torch.zeros((3, w.n_gas), dtype=torch.float32, device="cuda")
+        c.field(b.TFSPH_FIELD_VEL_G, out=out)
+        torch.cuda.synchronize()
+    assert np.array_equal(out.cpu().numpy().astype(np.float64), ref["gv"])
+
+
+def test_steps_are_deterministic():
+    w = workloads.box3d(nside=12, precision=0)
+    b = gpu_lib()
+    res = []
+    for _ in range(2):
+        with gpu_context(w) as c:
+            for _ in range(3):
+                c.step(w.tau, w.g)
+            res.append((c.field(b.TFSPH_FIELD_VEL_G), c.field(b.TFSPH_FIELD_POS_D)))
+    assert np.array_equal(res[0][0], res[1][0]) and np.array_equal(res[0][1], res[1][1])
+
+
+def test_set_state_restarts_the_run(orc):
+    b = gpu_lib()
+    w = workloads.dustywave(n=100, precision=1)
+    with gpu_context(w) as c:
+        c.step(w.tau, w.g)
+        c.step(w.tau, w.g)
+        c.set_state(w.gx, w.gv, w.dx, w.du, w.tstop)
+        assert c.info().steps == 0
+        c.step(w.tau, w.g)
+        gv = c.field(b.TFSPH_FIELD_VEL_G)
+    _, s, _, _ = _oracle_step(orc, w)
+    assert normwise(gv, s.gv) < 1e-12
+
+
+def test_dustywave_fp64_200_steps(orc):
+    """The full Dustywave run (100 + 100 particles, 200 steps, FP64) stays on
+    the oracle's trajectory."""
+    b = gpu_lib()
+    w = workloads.dustywave(precision=1)
+    p = oracle_params(w)
+    s = orc.make_state(p, w.gx, w.gv, w.dx, w.du, w.tstop)
+    with gpu_context(w) as c:
+        for _ in range(w.nsteps):
+            c.step(w.tau, w.g)
+            orc.step(p, s, w.tau, w.g)
+        gv = c.field(b.TFSPH_FIELD_VEL_G)
+        du = c.field(b.TFSPH_FIELD_VEL_D)
+    assert normwise(gv, s.gv) < 1e-9 and normwise(du, s.du) < 1e-9
+
+
+# ---------------------------------------------------------------------------
+# Full-size workloads, in the launch configuration the benchmark times
+# ---------------------------------------------------------------------------
+def test_box3d_full_size_one_step(orc):
+    """3D box, 128^3 gas + 128^3 dust: every output against the oracle."""
+    _compare(orc, workloads.box3d(nside=128, precision=0))
+
+
+def test_dustyshock_full_size_one_step(orc):
+    _compare(orc, workloads.dustyshock(precision=0))
+
+
+def test_column2d_full_size_one_step(orc):
+    _compare(orc, workloads.column2d(nside=512, precision=0))
