@@ -1,0 +1,442 @@
+#!/usr/bin/env python
+"""Benchmark of the GB300 SPH-IDIC step: gas+dust particle-updates per second.
+
+Default workload: the 3D periodic box, 128^3 gas + 128^3 dust particles
+(4,194,304 in total), h = 1.2 dx (about 58 neighbours), 128^3 cells,
+t_stop = 1e-4, FP32 state and pair sums with FP32 cell sums. A step is one
+full pass of the path (binning, density, force, implicit cell drag, update).
+
+  python bench.py [--gpus N] [--steps K] [--warmup W] [--workload box3d|dustyshock|column2d]
+                  [--impl ours|reference]
+
+Prints one JSON line (rank 0). Timed region: barrier + synchronize on both
+sides, CUDA events on the library's stream, max over ranks. The state of the
+default workload (~300 MB per step of traffic) is larger than L2, so L2 is not
+flushed. N > 1 runs one independent replica per GPU (weak scaling; the step
+has no data-path collective). ``--impl reference`` times the FP64 CPU oracle
+on a bounded sample of the same workload.
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import math
+import os
+import statistics
+import subprocess
+import sys
+import tempfile
+import time
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+if ROOT not in sys.path:
+    sys.path.insert(0, ROOT)
+
+METRIC = "gas+dust particle-updates/s per TFSPH step; % HBM roofline; adjoint/fwd time"
+UNIT = "particle-updates/s"
+
+
+def parse_args(argv=None):
+    ap = argparse.ArgumentParser(description=__doc__, formatter_class=argparse.RawDescriptionHelpFormatter)
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=20)
+    ap.add_argument("--warmup", type=int, default=5)
+    ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
+    ap.add_argument("--workload", choices=["box3d", "dustyshock", "column2d"], default="box3d")
+    ap.add_argument("--cell-acc", choices=["fp32", "fp64"], default="fp32")
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--no-e2e", action="store_true")
+    ap.add_argument("--no-clocks", action="store_true")
+    return ap.parse_args(argv)
+
+
+# ---------------------------------------------------------------------------
+# Distributed plumbing (replicas only)
+# ---------------------------------------------------------------------------
+class Dist:
+    def __init__(self):
+        self.rank = int(os.environ.get("RANK", "0"))
+        self.world = int(os.environ.get("WORLD_SIZE", "1"))
+        self.local_rank = int(os.environ.get("LOCAL_RANK", "0"))
+        self.pg = None
+
+    def init(self, backend: str):
+        if self.world > 1:
+            import torch.distributed as dist
+            os.environ.setdefault("MASTER_ADDR", "127.0.0.1")
+            dist.init_process_group(backend=backend, rank=self.rank, world_size=self.world)
+            self.pg = dist
+
+    def barrier(self):
+        if self.pg is not None:
+            self.pg.barrier()
+
+    def max(self, x: float) -> float:
+        if self.pg is None:
+            return x
+        import torch
+        dev = "cuda" if self.pg.get_backend() == "nccl" else "cpu"
+        t = torch.tensor([x], dtype=torch.float64, device=dev)
+        self.pg.all_reduce(t, op=self.pg.ReduceOp.MAX)
+        return float(t.item())
+
+    def sum(self, x: float) -> float:
+        if self.pg is None:
+            return x
+        import torch
+        dev = "cuda" if self.pg.get_backend() == "nccl" else "cpu"
+        t = torch.tensor([x], dtype=torch.float64, device=dev)
+        self.pg.all_reduce(t, op=self.pg.ReduceOp.SUM)
+        return float(t.item())
+
+    def close(self):
+        if self.pg is not None:
+            self.pg.destroy_process_group()
+
+
+# ---------------------------------------------------------------------------
+# Workloads
+# ---------------------------------------------------------------------------
+def make_workload(name: str, scale: int = 0):
+    import workloads
+    if name == "box3d":
+        nside = scale or 128
+        w = workloads.box3d(nside=nside, precision=0)
+        desc = (f"3D periodic box [0,1)^3, {nside}^3 gas + {nside}^3 dust, Gaussian random velocity "
+                f"fields (k^-2, rms 0.1 cs), h=1.2dx (~58 neighbours), {nside}^3 cells, t_stop=1e-4")
+    elif name == "dustyshock":
+        nl = scale or 177778
+        w = workloads.dustyshock(n_left=nl, n_right=max(1, nl // 8), precision=0)
+        desc = (f"1D dusty Sod shock tube with walls, {w.n_gas} gas (incl. frozen walls) + {w.n_dust} dust, "
+                f"rho 1/0.125, p 1/0.1, gamma 1.4, dust-to-gas 1, t_stop log-uniform 1e-5..1, cell 2h")
+    else:
+        nside = scale or 512
+        w = workloads.column2d(nside=nside, precision=0)
+        desc = (f"2D dust settling column, {nside}^2 gas (+ frozen walls) + {nside}^2 dust, g=(0,-1), "
+                f"t_stop log-uniform 1e-3..1e-1, cell 2h")
+    return w, desc
+
+
+# ---------------------------------------------------------------------------
+# Clock sampling during the timed region
+# ---------------------------------------------------------------------------
+class Clocks:
+    QUERY = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+             "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+             "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, device_index: str):
+        self.dev = device_index
+        self.proc = None
+        self.path = None
+
+    def start(self):
+        try:
+            fd, self.path = tempfile.mkstemp(prefix="clocks_", suffix=".csv")
+            os.close(fd)
+            self.proc = subprocess.Popen(
+                ["nvidia-smi", "-i", self.dev, f"--query-gpu={self.QUERY}", "--format=csv,noheader,nounits",
+                 "-lms", "200", "-f", self.path], stdout=subprocess.DEVNULL, stderr=subprocess.DEVNULL)
+        except (OSError, FileNotFoundError):
+            self.proc = None
+
+    def stop(self) -> dict:
+        if self.proc is None:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["nvidia-smi unavailable"]}
+        time.sleep(0.25)
+        self.proc.terminate()
+        try:
+            self.proc.wait(timeout=5)
+        except subprocess.TimeoutExpired:
+            self.proc.kill()
+        sm, smax, reasons = [], [], set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        try:
+            with open(self.path) as f:
+                for line in f:
+                    parts = [x.strip() for x in line.split(",")]
+                    if len(parts) < 9:
+                        continue
+                    try:
+                        sm.append(float(parts[1]))
+                        smax.append(float(parts[2]))
+                    except ValueError:
+                        continue
+                    for nm, val in zip(names, parts[5:9]):
+                        if val.lower() == "active":
+                            reasons.add(nm)
+            os.unlink(self.path)
+        except OSError:
+            pass
+        return {"sm_mhz": statistics.median(sm) if sm else None,
+                "sm_max_mhz": max(smax) if smax else None,
+                "samples": len(sm), "reasons": sorted(reasons)}
+
+
+# ---------------------------------------------------------------------------
+# Roofline bookkeeping (algorithmic bytes / flops per phase)
+# ---------------------------------------------------------------------------
+def algorithmic(phase: str, w, info, nb_mean: float) -> tuple[str, float]:
+    """(bound, algorithmic bytes or flops of one launch of the phase's kernel).
+
+    Bytes count each array the kernel must touch once (FP32 state: V4 = 16 B);
+    flops count neighbour pairs only (density 20, force 35 flops per pair).
+    """
+    ng, nd = w.n_gas, w.n_dust
+    n = ng + nd
+    nc = info.n_cells_total
+    if phase == "count":
+        return "hbm", 4.0 * n + 2 * 8.0 * nc
+    if phase == "scan":
+        return "hbm", 2 * (4.0 + 4.0 + 4.0) * nc
+    if phase == "scatter":
+        return "hbm", 16.0 * n + 2 * 12.0 * nc
+    if phase == "gather":
+        return "hbm", 84.0 * n
+    if phase == "drag":
+        return "hbm", (16 + 16 + 16 + 16 + 16 + 4) * ng + (16 + 16 + 16 + 16 + 4) * nd + 2 * 8.0 * nc
+    if phase == "density":
+        return "alu", 20.0 * nb_mean * ng
+    if phase == "force":
+        return "alu", 35.0 * nb_mean * ng
+    raise ValueError(phase)
+
+
+def peaks():
+    path = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    try:
+        with open(path) as f:
+            pk = json.load(f)
+        return pk, "measured"
+    except (OSError, ValueError):
+        return {"hbm_gbs": 6800.0, "sm_max_mhz": 2070.0}, "fallback"
+
+
+def fp32_alu_peak_tflops(sm_count: int, mhz: float) -> float:
+    """FP32 FMA pipes: 128 lanes per SM, 2 flops per FMA."""
+    return sm_count * 128 * 2 * mhz * 1e6 / 1e12
+
+
+# ---------------------------------------------------------------------------
+# CPU baseline: the FP64 oracle, as it stands
+# ---------------------------------------------------------------------------
+def oracle_sample(workload: str, scale: int):
+    import oracle
+    w, desc = make_workload(workload, scale)
+    q = w.params
+    p = oracle.Params(dim=q["dim"], lo=q["lo"], hi=q["hi"], periodic=q["periodic"], h=q["h"],
+                      cell_size=q["cell_size"], m_gas=q["m_gas"], m_dust=q["m_dust"], eos=q["eos"],
+                      cs=q["cs"], gamma=q["gamma"], av_alpha=q["av_alpha"], av_beta=q["av_beta"],
+                      tstar_mode=q["tstar_mode"], decide_fp32=1)
+    s = oracle.make_state(p, w.gx, w.gv, w.dx, w.du, w.tstop, ge=w.ge, frozen=w.frozen)
+    return oracle, p, s, w, desc
+
+
+def cpu_baseline(workload: str, scale: int, steps: int = 1) -> dict:
+    oracle, p, s, w, desc = oracle_sample(workload, scale)
+    oracle.build()
+    t0 = time.perf_counter()
+    for _ in range(steps):
+        oracle.step(p, s, w.tau, w.g)
+    dt = time.perf_counter() - t0
+    n = w.n_gas + w.n_dust
+    return {"value": n * steps / dt, "unit": UNIT, "cores": oracle.omp_threads(), "kind": "oracle",
+            "sample": f"{steps} FP64 oracle step(s) of {desc} ({n} particles), {dt:.2f} s wall"}
+
+
+def run_reference(args, dist: Dist):
+    """The oracle timed as the reference arm (rank 0 only)."""
+    if dist.rank != 0:
+        return
+    scale = {"box3d": 48, "dustyshock": 20000, "column2d": 128}[args.workload]
+    oracle, p, s, w, desc = oracle_sample(args.workload, scale)
+    oracle.build()
+    for _ in range(args.warmup):
+        oracle.step(p, s, w.tau, w.g)
+    t0 = time.perf_counter()
+    for _ in range(args.steps):
+        oracle.step(p, s, w.tau, w.g)
+    dt = time.perf_counter() - t0
+    n = w.n_gas + w.n_dust
+    value = n * args.steps / dt
+    cores = oracle.omp_threads()
+    line = {
+        "impl": "reference", "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": args.gpus,
+        "steps": args.steps, "warmup": args.warmup, "ms_per_step": dt / args.steps * 1e3,
+        "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+        "config": {"workload": args.workload, "sample": desc, "particles": n},
+        "cpu_baseline": {"value": value, "unit": UNIT, "cores": cores, "kind": "oracle",
+                         "sample": f"{args.steps} timed FP64 oracle steps of {desc}"},
+        "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
+    }
+    print(json.dumps(line), flush=True)
+
+
+# ---------------------------------------------------------------------------
+# Our arm
+# ---------------------------------------------------------------------------
+def run_ours(args, dist: Dist):
+    import numpy as np
+    import torch
+
+    from paper_1908_01682_gb300 import binding as b
+
+    if not torch.cuda.is_available():
+        raise SystemExit("bench.py: no CUDA device; the GPU path has no CPU fallback")
+    torch.cuda.set_device(dist.local_rank % torch.cuda.device_count())
+    visible = [v for v in os.environ.get("CUDA_VISIBLE_DEVICES", "").split(",") if v.strip()]
+    dev_index = visible[dist.local_rank % len(visible)] if visible else str(torch.cuda.current_device())
+
+    w, desc = make_workload(args.workload)
+    cell_acc = b.TFSPH_CELL_ACC_FP32 if args.cell_acc == "fp32" else b.TFSPH_CELL_ACC_FP64
+    p = b.params_from_dict(w.params, cell_acc=cell_acc)
+    f32 = lambda a: None if a is None else np.ascontiguousarray(a, dtype=np.float32)
+    ctx = b.Context(p, f32(w.gx), f32(w.gv), f32(w.dx), f32(w.du), f32(w.tstop), ge=f32(w.ge), frozen=w.frozen)
+    stream = torch.cuda.current_stream()
+    ctx.set_stream(stream)
+    info = ctx.info()
+    n = w.n_gas + w.n_dust
+
+    # neighbour statistics of the input (for the algorithmic flop count)
+    nb_mean = float(np.mean(ctx.debug(b.TFSPH_DEBUG_NEIGH_COUNT))) if w.n_gas else 0.0
+
+    for _ in range(args.warmup):
+        ctx.step(w.tau, w.g)
+    torch.cuda.synchronize()
+
+    # ---- timed region (headline) ----
+    clocks = Clocks(dev_index)
+    if not args.no_clocks:
+        clocks.start()
+    launches0 = ctx.info().launches
+    dist.barrier()
+    torch.cuda.synchronize()
+    e0 = torch.cuda.Event(enable_timing=True)
+    e1 = torch.cuda.Event(enable_timing=True)
+    e0.record(stream)
+    for _ in range(args.steps):
+        ctx.step(w.tau, w.g)
+    e1.record(stream)
+    torch.cuda.synchronize()
+    dist.barrier()
+    ms_total = e0.elapsed_time(e1)
+    clk = clocks.stop() if not args.no_clocks else {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["not sampled"]}
+    launches = ctx.info().launches - launches0
+    ctx.sync()
+    ms_total_max = dist.max(ms_total)
+    ms_per_step = ms_total_max / args.steps
+    value = dist.sum(n * args.steps) / (ms_total_max / 1e3)
+
+    # ---- profiled pass: per-phase CUDA events on the same stream ----
+    ctx.profile(True)
+    for _ in range(args.steps):
+        ctx.step(w.tau, w.g)
+    phase_ms, psteps, _ = ctx.profile_read()
+    ctx.profile(False)
+    phase_avg = {k: v / max(1, psteps) for k, v in phase_ms.items()}
+    dominant = max(phase_avg, key=phase_avg.get)
+    bound, amount = algorithmic(dominant, w, info, nb_mean)
+    pk, pk_src = peaks()
+    sm_count = torch.cuda.get_device_properties(0).multi_processor_count
+    if bound == "hbm":
+        achieved = amount / (phase_avg[dominant] * 1e-3) / 1e9
+        peak = float(pk.get("hbm_gbs", 6800.0))
+        unit = "GB/s"
+    else:
+        mhz = clk.get("sm_mhz") or float(pk.get("clocks_under_load", {}).get("sm_mhz_median", 0) or 0) \
+            or float(pk.get("sm_max_mhz", 2070.0))
+        achieved = amount / (phase_avg[dominant] * 1e-3) / 1e12
+        peak = fp32_alu_peak_tflops(sm_count, mhz)
+        unit = "TFLOP/s"
+    step_bytes = sum(algorithmic(ph, w, info, nb_mean)[1] for ph in ("count", "scan", "scatter", "gather", "drag")) \
+        + (24.0 + 32.0) * w.n_gas
+    roof = {"kernel": dominant, "bound": bound, "achieved": achieved, "peak": peak, "unit": unit,
+            "frac": achieved / peak, "traffic": None,
+            "peak_source": f"{pk_src}" + ("" if bound == "hbm" else f" (FP32 FMA lanes x {sm_count} SMs x SM clock)"),
+            "step_hbm_frac": (step_bytes / (ms_per_step * 1e-3) / 1e9) / float(pk.get("hbm_gbs", 6800.0)),
+            "step_algorithmic_bytes": step_bytes}
+
+    # ---- end to end through the C ABI with host buffers ----
+    e2e = None
+    if not args.no_e2e:
+        e2e = run_e2e(b, ctx, w, args, dist)
+
+    cpu = None
+    if dist.rank == 0 and dist.world == 1 and not args.no_cpu_baseline:
+        cpu = cpu_baseline(args.workload, 0)
+
+    ctx.close()
+    line = {
+        "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": dist.world, "steps": args.steps,
+        "warmup": args.warmup, "ms_per_step": ms_per_step, "higher_is_better": True, "scaling": "weak",
+        "vs_baseline": None, "dtype": "f32", "data": "synthetic",
+        "config": {"workload": args.workload, "description": desc, "n_gas": w.n_gas, "n_dust": w.n_dust,
+                   "cells": int(info.n_cells_total), "cell_sums": args.cell_acc, "tau": w.tau,
+                   "l2": "inputs larger than L2 (no flush)", "parallelism": f"replicas x{dist.world}"},
+        "clocks": clk, "e2e": e2e, "gpu_launches": int(launches),
+        "roofline": roof,
+        "kernel_ms": {k: round(v, 5) for k, v in phase_avg.items()},
+        "cpu_baseline": cpu,
+    }
+    if dist.rank == 0:
+        print(json.dumps(line), flush=True)
+
+
+def run_e2e(b, ctx, w, args, dist):
+    """Same metric through the public API with pinned host buffers: per step,
+    upload the state (tfsph_set_state), step, and read the new state back."""
+    import numpy as np
+    import torch
+
+    def pinned(a):
+        t = torch.empty(a.shape, dtype=torch.float32, pin_memory=True)
+        t.numpy()[...] = a
+        return t
+
+    keep = [pinned(w.gx), pinned(w.gv), pinned(w.dx), pinned(w.du), pinned(w.tstop)]
+    ge = pinned(w.ge) if w.ge is not None else None
+    gx, gv, dx, du, ts = (t.numpy() for t in keep)
+    outs = {f: torch.empty((w.dim, w.n_gas if f in (b.TFSPH_FIELD_POS_G, b.TFSPH_FIELD_VEL_G) else w.n_dust),
+                           dtype=torch.float32, pin_memory=True)
+            for f in (b.TFSPH_FIELD_POS_G, b.TFSPH_FIELD_VEL_G, b.TFSPH_FIELD_POS_D, b.TFSPH_FIELD_VEL_D)}
+    h2d = 4 * (gx.size + gv.size + dx.size + du.size + ts.size + (w.n_gas if ge is not None else 0)) + \
+        (w.n_gas if w.frozen is not None else 0)
+    d2h = sum(4 * t.numel() for t in outs.values())
+
+    def one():
+        ctx.set_state(gx, gv, dx, du, ts, ge=None if ge is None else ge.numpy(), frozen=w.frozen)
+        ctx.step(w.tau, w.g)
+        for f, t in outs.items():
+            ctx.field(f, out=t.numpy())
+
+    one()
+    k = max(1, min(args.steps, 10))
+    dist.barrier()
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    for _ in range(k):
+        one()
+    torch.cuda.synchronize()
+    dt = dist.max(time.perf_counter() - t0)
+    dist.barrier()
+    n = w.n_gas + w.n_dust
+    return {"value": dist.sum(n * k) / dt, "unit": UNIT, "h2d_bytes_per_step": int(h2d),
+            "d2h_bytes_per_step": int(d2h), "steps": k, "ms_per_step": dt / k * 1e3}
+
+
+def main(argv=None):
+    args = parse_args(argv)
+    dist = Dist()
+    if args.impl == "reference":
+        run_reference(args, dist)  # rank 0 only; the other ranks exit without work
+        return
+    import torch
+    dist.init("nccl" if torch.cuda.is_available() else "gloo")
+    try:
+        run_ours(args, dist)
+    finally:
+        dist.close()
+
+
+if __name__ == "__main__":
+    main()

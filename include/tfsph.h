@@ -122,7 +122,18 @@ typedef struct {
     int64_t n_cells_total;
     int64_t steps;         /* steps taken since init or the last set_state */
     int64_t device_bytes;  /* device memory held by the context */
+    int64_t launches;      /* kernels launched by tfsph_step since init */
 } tfsph_info_t;
+
+/* phases timed by tfsph_profile_read */
+#define TFSPH_PROF_COUNT   0  /* cell counts (atomics) */
+#define TFSPH_PROF_SCAN    1  /* exclusive scan of the counts: cell ranges */
+#define TFSPH_PROF_SCATTER 2  /* slot per particle */
+#define TFSPH_PROF_GATHER  3  /* rank in cell by id, copy into cell order */
+#define TFSPH_PROF_DENSITY 4  /* gas summation density and p/rho^2 */
+#define TFSPH_PROF_FORCE   5  /* gas pressure (+ viscous) acceleration */
+#define TFSPH_PROF_DRAG    6  /* implicit cell drag, particle update, next keys */
+#define TFSPH_PROF_NPHASE  7
 
 /* Create a context from a particle state (Sec. 2.3 set-up).
  *   gas[]:  2*dim arrays of n_gas values, x_0..x_{dim-1}, v_0..v_{dim-1},
@@ -170,6 +181,15 @@ int tfsph_debug(tfsph_ctx *c, int what, void *out, int mem_kind);
 
 /* Sizes and counters of a context. */
 int tfsph_info(const tfsph_ctx *c, tfsph_info_t *out);
+
+/* Start (enable = 1, clearing the totals) or stop (0) timing the phases of
+ * tfsph_step with CUDA events recorded on the context's stream. */
+int tfsph_profile(tfsph_ctx *c, int enable);
+
+/* Synchronise and read the accumulated time per phase (TFSPH_PROF_*, ms,
+ * TFSPH_PROF_NPHASE doubles), the number of timed steps and the kernels
+ * those steps launched. Any pointer may be NULL. */
+int tfsph_profile_read(tfsph_ctx *c, double *ms, int64_t *steps, int64_t *launches);
 
 /* Wait for the context's stream and report any error raised on the device
  * since the last call (NONFINITE for bad t_stop values, INTERNAL otherwise). */

@@ -50,7 +50,7 @@ class _Params(C.Structure):
 
 class _StepOut(C.Structure):
     _fields_ = [
-        ("rho_g", C.c_void_p), ("acc_g", C.c_void_p), ("dedt_g", C.c_void_p),
+        ("rho_g", C.c_void_p), ("acc_g", C.c_void_p), ("dedt_g", C.c_void_p), ("acc_scale_g", C.c_void_p),
         ("nb_count", C.c_void_p), ("nb_fprint", C.c_void_p),
         ("keys_g", C.c_void_p), ("keys_d", C.c_void_p),
         ("perm_g", C.c_void_p), ("perm_d", C.c_void_p),
@@ -74,7 +74,7 @@ def _load():
         _lib.orc_ncell.argtypes = [vp, vp]
         _lib.orc_bin.argtypes = [vp, i64, vp, vp, vp, vp]
         _lib.orc_density.argtypes = [vp, i64, vp, d, vp, vp, vp]
-        _lib.orc_accel.argtypes = [vp, i64, vp, vp, vp, vp, vp, vp]
+        _lib.orc_accel.argtypes = [vp, i64, vp, vp, vp, vp, vp, vp, vp]
         _lib.orc_max_dt.restype = d
         _lib.orc_max_dt.argtypes = [vp, i64, vp, vp, vp, d]
         _lib.orc_step.argtypes = [vp, i64, i64, vp, vp, vp, vp, vp, vp, vp, d, vp, vp, vp]
@@ -164,7 +164,9 @@ def density(p: Params, x, m: float):
     return rho, cnt, fp
 
 
-def accel(p: Params, x, v, e, rho):
+def accel(p: Params, x, v, e, rho, with_scale: bool = False):
+    """Pressure (+ viscous) acceleration and energy rate; with_scale also
+    returns the per-particle magnitude sum of the pair terms."""
     x = _f64(x, (p.dim, -1))
     n = x.shape[1]
     v = _f64(v, (p.dim, n))
@@ -172,9 +174,11 @@ def accel(p: Params, x, v, e, rho):
     rho = _f64(rho, (n,))
     acc = np.zeros((p.dim, n))
     dedt = np.zeros(n)
+    scale = np.zeros(n)
     pc = p.c()
-    _load().orc_accel(C.byref(pc), n, _ptr(x), _ptr(v), _ptr(e), _ptr(rho), _ptr(acc), _ptr(dedt))
-    return acc, dedt
+    _load().orc_accel(C.byref(pc), n, _ptr(x), _ptr(v), _ptr(e), _ptr(rho), _ptr(acc), _ptr(dedt),
+                      _ptr(scale))
+    return (acc, dedt, scale) if with_scale else (acc, dedt)
 
 
 def max_dt(p: Params, v, e=None, frozen=None, cfl: float = 0.3) -> float:
@@ -208,6 +212,7 @@ class StepResult:
     rho_g: np.ndarray
     acc_g: np.ndarray
     dedt_g: np.ndarray
+    acc_scale_g: np.ndarray
     nb_count: np.ndarray
     nb_fprint: np.ndarray
     keys_g: np.ndarray
@@ -238,11 +243,12 @@ def step(p: Params, s: State, tau: float, g=(0.0, 0.0, 0.0), acc_override=None) 
     nd = s.dx.shape[1]
     nc = ncell(p)
     ncells = int(np.prod(nc))
-    r = StepResult(np.zeros(ng), np.zeros((p.dim, ng)), np.zeros(ng), np.zeros(ng, np.int64),
+    r = StepResult(np.zeros(ng), np.zeros((p.dim, ng)), np.zeros(ng), np.zeros(ng), np.zeros(ng, np.int64),
                    np.zeros(ng, np.uint64), np.zeros(ng, np.int64), np.zeros(nd, np.int64),
                    np.zeros(ng, np.int64), np.zeros(nd, np.int64),
                    np.zeros(ncells + 1, np.int64), np.zeros(ncells + 1, np.int64), 0)
-    out = _StepOut(_ptr(r.rho_g), _ptr(r.acc_g), _ptr(r.dedt_g), _ptr(r.nb_count), _ptr(r.nb_fprint),
+    out = _StepOut(_ptr(r.rho_g), _ptr(r.acc_g), _ptr(r.dedt_g), _ptr(r.acc_scale_g), _ptr(r.nb_count),
+                   _ptr(r.nb_fprint),
                    _ptr(r.keys_g), _ptr(r.keys_d), _ptr(r.perm_g), _ptr(r.perm_d),
                    _ptr(r.cstart_g), _ptr(r.cstart_d), 0)
     g3 = (C.c_double * 3)(*[float(g[k]) if k < len(g) else 0.0 for k in range(3)])

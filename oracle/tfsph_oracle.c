@@ -142,7 +142,37 @@ static int64_t orc_key(const orc_params *P, const int32_t nc[3], const double x[
 /* ------------------------------------------------------------------------ */
 /* Pair geometry. Membership r^2 < (2h)^2 decided in the path's precision.   */
 /* d[] receives x_a - x_b (minimum image on periodic axes) in binary64.      */
+/*                                                                          */
+/* The decision's displacement along an axis is s = x_a - x_b; when |s|     */
+/* exceeds half the box, the image shift is applied to s (exact: s and L    */
+/* are within a factor of two) and the rounding error of s, recovered with  */
+/* Knuth's two-sum, is added back, so that pairs across the periodic seam   */
+/* lose no more precision than any other pair.                              */
 /* ------------------------------------------------------------------------ */
+static float orc_disp32(float xa, float xb, int per, float L, float half)
+{
+    float s = xa - xb;
+    if (per && (s > half || s < -half)) {
+        float bb = s - xa;
+        float e = (xa - (s - bb)) + (-xb - bb);
+        float t = s > half ? s - L : s + L;
+        return t + e;
+    }
+    return s;
+}
+
+static double orc_disp64(double xa, double xb, int per, double L, double half)
+{
+    double s = xa - xb;
+    if (per && (s > half || s < -half)) {
+        double bb = s - xa;
+        double e = (xa - (s - bb)) + (-xb - bb);
+        double t = s > half ? s - L : s + L;
+        return t + e;
+    }
+    return s;
+}
+
 static int orc_pair(const orc_params *P, const double xa[3], const double xb[3],
                     double d[3], double *r2)
 {
@@ -150,13 +180,9 @@ static int orc_pair(const orc_params *P, const double xa[3], const double xb[3],
     if (P->decide_fp32) {
         float acc = 0.0f;
         for (int k = 0; k < P->dim; ++k) {
-            float dx = (float)xa[k] - (float)xb[k];
-            if (P->periodic[k]) {
-                float L = (float)(P->hi[k] - P->lo[k]);
-                float half = (float)(0.5 * (P->hi[k] - P->lo[k]));
-                if (dx > half) dx = dx - L;
-                else if (dx < -half) dx = dx + L;
-            }
+            float L = (float)(P->hi[k] - P->lo[k]);
+            float half = (float)(0.5 * (P->hi[k] - P->lo[k]));
+            float dx = orc_disp32((float)xa[k], (float)xb[k], P->periodic[k], L, half);
             float sq = dx * dx;
             acc = (k == 0) ? sq : acc + sq;
         }
@@ -165,13 +191,9 @@ static int orc_pair(const orc_params *P, const double xa[3], const double xb[3],
     } else {
         double acc = 0.0;
         for (int k = 0; k < P->dim; ++k) {
-            double dx = xa[k] - xb[k];
-            if (P->periodic[k]) {
-                double L = P->hi[k] - P->lo[k];
-                double half = 0.5 * (P->hi[k] - P->lo[k]);
-                if (dx > half) dx = dx - L;
-                else if (dx < -half) dx = dx + L;
-            }
+            double L = P->hi[k] - P->lo[k];
+            double half = 0.5 * (P->hi[k] - P->lo[k]);
+            double dx = orc_disp64(xa[k], xb[k], P->periodic[k], L, half);
             double sq = dx * dx;
             acc = (k == 0) ? sq : acc + sq;
         }
@@ -181,12 +203,8 @@ static int orc_pair(const orc_params *P, const double xa[3], const double xb[3],
     for (int k = 0; k < 3; ++k) {
         d[k] = 0.0;
         if (k >= P->dim) continue;
-        double dx = xa[k] - xb[k];
-        if (P->periodic[k]) {
-            double L = P->hi[k] - P->lo[k];
-            if (dx > 0.5 * L) dx -= L;
-            else if (dx < -0.5 * L) dx += L;
-        }
+        double L = P->hi[k] - P->lo[k];
+        double dx = orc_disp64(xa[k], xb[k], P->periodic[k], L, 0.5 * L);
         d[k] = dx;
         s += dx * dx;
     }
@@ -407,6 +425,7 @@ typedef struct {
     const double *v, *rho, *pr, *cs;
     double acc[3];
     double dedt;
+    double scale;  /* sum over pairs of |pair coefficient| |grad W|: the condition scale of A */
 } orc_force_ctx;
 
 static void orc_force_visit(void *vctx, int64_t b)
@@ -439,17 +458,20 @@ static void orc_force_visit(void *vctx, int64_t b)
         pi = (-P->av_alpha * cbar * mu + P->av_beta * mu * mu) / rbar;
     }
     double m = P->m_gas;
-    double vg = 0.0;
+    double vg = 0.0, g2 = 0.0;
     for (int k = 0; k < P->dim; ++k) {
         c->acc[k] -= m * (qa + qb + pi) * grad[k];
         vg += vab[k] * grad[k];
+        g2 += grad[k] * grad[k];
     }
     c->dedt += m * (qa + 0.5 * pi) * vg;
+    c->scale += m * fabs(qa + qb + pi) * sqrt(g2);
 }
 
-/* acc[dim*n], dedt[n] (nullable) for every gas particle. */
+/* acc[dim*n], dedt[n] (nullable) and scale[n] (nullable: the magnitude sum
+ * of the pair terms, a diagnostic for tests) for every gas particle. */
 int orc_accel(const orc_params *P, int64_t n, const double *x, const double *v,
-              const double *e, const double *rho, double *acc, double *dedt)
+              const double *e, const double *rho, double *acc, double *dedt, double *scale)
 {
     orc_grid G;
     int64_t *perm = NULL, *cstart = NULL;
@@ -477,9 +499,11 @@ int orc_accel(const orc_params *P, int64_t n, const double *x, const double *v,
         c.cs = cs;
         c.acc[0] = c.acc[1] = c.acc[2] = 0.0;
         c.dedt = 0.0;
+        c.scale = 0.0;
         orc_foreach_candidate(&G, c.pa, orc_force_visit, &c);
         for (int k = 0; k < P->dim; ++k) acc[(int64_t)k * n + a] = c.acc[k];
         if (dedt) dedt[a] = c.dedt;
+        if (scale) scale[a] = c.scale;
     }
     free(pr);
     free(cs);
@@ -540,6 +564,7 @@ typedef struct {
     double *rho_g;          /* [ng] density used in the step */
     double *acc_g;          /* [dim*ng] pressure (+viscous) acceleration */
     double *dedt_g;         /* [ng] */
+    double *acc_scale_g;    /* [ng] magnitude sum of the pair terms of A (diagnostic) */
     int64_t *nb_count;      /* [ng] */
     uint64_t *nb_fprint;    /* [ng] */
     int64_t *keys_g, *keys_d;     /* [ng], [nd] per particle (id order) */
@@ -591,7 +616,7 @@ int orc_step(const orc_params *P, int64_t ng, int64_t nd,
                             out ? out->nb_fprint : NULL);
 
     /* 3. Gas pressure (+ viscous) acceleration and energy rate. */
-    if (ng > 0) orc_accel(P, ng, gx, gv, ge, rho, acc, dedt);
+    if (ng > 0) orc_accel(P, ng, gx, gv, ge, rho, acc, dedt, out ? out->acc_scale_g : NULL);
     if (acc_override) memcpy(acc, acc_override, sizeof(double) * (size_t)(dim * ng));
 
     /* 4. Cell aggregates (Eqs. 17, 21), summed in sorted order. */

@@ -30,6 +30,8 @@ TFSPH_CELL_ACC_FP32, TFSPH_CELL_ACC_FP64 = 0, 1
 (TFSPH_FIELD_POS_G, TFSPH_FIELD_VEL_G, TFSPH_FIELD_ENERGY_G, TFSPH_FIELD_RHO_G, TFSPH_FIELD_POS_D,
  TFSPH_FIELD_VEL_D, TFSPH_FIELD_TSTOP_D, TFSPH_FIELD_RHO_D) = range(8)
 TFSPH_ORDER_ORIGINAL, TFSPH_ORDER_CELL = 0, 1
+PROF_PHASES = ("count", "scan", "scatter", "gather", "density", "force", "drag")
+TFSPH_PROF_NPHASE = len(PROF_PHASES)
 (TFSPH_DEBUG_KEYS_G, TFSPH_DEBUG_KEYS_D, TFSPH_DEBUG_PERM_G, TFSPH_DEBUG_PERM_D, TFSPH_DEBUG_CSTART_G,
  TFSPH_DEBUG_CSTART_D, TFSPH_DEBUG_NEIGH_COUNT, TFSPH_DEBUG_NEIGH_FPRINT, TFSPH_DEBUG_ACC_G) = range(9)
 
@@ -49,6 +51,7 @@ class tfsph_info_t(C.Structure):
     _fields_ = [
         ("n_gas", C.c_int64), ("n_dust", C.c_int64), ("n_cells", C.c_int32 * 3), ("reach", C.c_int32 * 3),
         ("n_cells_total", C.c_int64), ("steps", C.c_int64), ("device_bytes", C.c_int64),
+        ("launches", C.c_int64),
     ]
 
 
@@ -88,6 +91,8 @@ def load() -> C.CDLL:
     lib.tfsph_debug.argtypes = [ctxp, i32, vp, i32]
     lib.tfsph_info.argtypes = [ctxp, C.POINTER(tfsph_info_t)]
     lib.tfsph_sync.argtypes = [ctxp]
+    lib.tfsph_profile.argtypes = [ctxp, i32]
+    lib.tfsph_profile_read.argtypes = [ctxp, vp, vp, vp]
     lib.tfsph_last_error.argtypes = [ctxp]
     lib.tfsph_last_error.restype = C.c_char_p
     lib.tfsph_status_string.argtypes = [i32]
@@ -96,7 +101,8 @@ def load() -> C.CDLL:
     lib.tfsph_destroy.restype = None
     lib.tfsph_version.argtypes = []
     for name in ("tfsph_init", "tfsph_set_state", "tfsph_set_stream", "tfsph_step", "tfsph_max_dt",
-                 "tfsph_fields", "tfsph_debug", "tfsph_info", "tfsph_sync", "tfsph_version"):
+                 "tfsph_fields", "tfsph_debug", "tfsph_info", "tfsph_sync", "tfsph_version",
+                 "tfsph_profile", "tfsph_profile_read"):
         getattr(lib, name).restype = C.c_int
     _lib = lib
     return lib
@@ -153,6 +159,20 @@ def tfsph_info(ctx):
 
 def tfsph_sync(ctx) -> int:
     return load().tfsph_sync(ctx)
+
+
+def tfsph_profile(ctx, enable: int) -> int:
+    return load().tfsph_profile(ctx, int(enable))
+
+
+def tfsph_profile_read(ctx):
+    """Returns (status, per-phase ms array, timed steps, kernel launches)."""
+    ms = (C.c_double * TFSPH_PROF_NPHASE)()
+    steps = C.c_int64(0)
+    launches = C.c_int64(0)
+    rc = load().tfsph_profile_read(ctx, C.cast(ms, C.c_void_p), C.cast(C.pointer(steps), C.c_void_p),
+                                   C.cast(C.pointer(launches), C.c_void_p))
+    return rc, np.array(ms[:], dtype=np.float64), steps.value, launches.value
 
 
 def tfsph_last_error(ctx) -> str:
@@ -305,6 +325,15 @@ class Context:
 
     def sync(self):
         _check(tfsph_sync(self.ctx), self.ctx)
+
+    def profile(self, enable: bool = True):
+        _check(tfsph_profile(self.ctx, 1 if enable else 0), self.ctx)
+
+    def profile_read(self):
+        """(dict phase -> total ms, timed steps, kernel launches)."""
+        rc, ms, steps, launches = tfsph_profile_read(self.ctx)
+        _check(rc, self.ctx)
+        return dict(zip(PROF_PHASES, ms.tolist())), steps, launches
 
     def close(self):
         if getattr(self, "ctx", None):

@@ -351,15 +351,18 @@ cudaError_t bin_t(const LaunchCtx &L, const void *geo, PhaseBufs &G, PhaseBufs &
     const uint32_t ncells = Gm.ncells;
     if (ntot > 0)
         k_count<<<grid_for(ntot, 256), 256, 0, L.stream>>>(G.key, ng, G.count, D.key, nd, D.count);
+    if (L.ev) cudaEventRecord(L.ev[1], L.stream);
     dim3 sg((unsigned)nblk, 2);
     k_scan_reduce<<<sg, kScanThreads, 0, L.stream>>>(G.count, D.count, ncells, bsum, (uint32_t)nblk);
     k_scan_top<<<2, kScanThreads, 0, L.stream>>>(bsum, (uint32_t)nblk);
     k_scan_down<<<sg, kScanThreads, 0, L.stream>>>(G.count, D.count, ncells, bsum, (uint32_t)nblk, G.start,
                                                    D.start, (uint32_t)ng, (uint32_t)nd);
+    if (L.ev) cudaEventRecord(L.ev[2], L.stream);
     if (ntot > 0) {
         k_scatter<<<grid_for(ntot, 256), 256, 0, L.stream>>>(G.key, G.id[G.cur], G.count, G.start, G.tmp_src,
                                                              G.tmp_id, ng, D.key, D.id[D.cur], D.count, D.start,
                                                              D.tmp_src, D.tmp_id, nd, L.d_err);
+        if (L.ev) cudaEventRecord(L.ev[3], L.stream);
         const int og = G.cur ^ 1, od = D.cur ^ 1;
         k_rank_gather<T><<<grid_for(ntot, 256), 256, 0, L.stream>>>(
             G.key, G.start, G.tmp_src, G.tmp_id, static_cast<const V4<T> *>(G.pos[G.cur]),
@@ -369,7 +372,10 @@ cudaError_t bin_t(const LaunchCtx &L, const void *geo, PhaseBufs &G, PhaseBufs &
             static_cast<V4<T> *>(D.pos[od]), static_cast<V4<T> *>(D.vel[od]), D.id[od], nd, L.d_err);
         G.cur = og;
         D.cur = od;
+    } else if (L.ev) {
+        cudaEventRecord(L.ev[3], L.stream);
     }
+    if (L.ev) cudaEventRecord(L.ev[4], L.stream);
     return cudaGetLastError();
 }
 

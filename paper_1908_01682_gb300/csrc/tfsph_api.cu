@@ -49,6 +49,14 @@ struct tfsph_ctx {
     bool has_frozen = false;
     int64_t steps = 0;
     int64_t device_bytes = 0;
+    int64_t launches = 0;
+    // phase timing: one set of TFSPH_PROF_NPHASE + 1 events per profiled step
+    bool profiling = false;
+    std::vector<std::vector<cudaEvent_t>> prof_sets;
+    size_t prof_used = 0;
+    double prof_ms[TFSPH_PROF_NPHASE] = {0};
+    int64_t prof_steps = 0;
+    int64_t prof_launches = 0;
     std::vector<void *> allocs;
     std::string err;
 };
@@ -160,6 +168,7 @@ LaunchCtx lctx(const tfsph_ctx *c)
     L.precision = c->precision;
     L.dim = c->dim;
     L.d_err = c->d_err;
+    L.ev = nullptr;
     return L;
 }
 
@@ -276,10 +285,49 @@ int load_state(tfsph_ctx *c, const void *const *gas, const void *const *dust, co
     return TFSPH_OK;
 }
 
-int prepare(tfsph_ctx *c)
+int fold_profile(tfsph_ctx *c)
 {
-    if (c->prepared) return TFSPH_OK;
+    if (c->prof_used == 0) return TFSPH_OK;
+    TF_CUDA(c, cudaStreamSynchronize(c->stream));
+    for (size_t k = 0; k < c->prof_used; ++k) {
+        auto &ev = c->prof_sets[k];
+        for (int ph = 0; ph < TFSPH_PROF_NPHASE; ++ph) {
+            float ms = 0.f;
+            TF_CUDA(c, cudaEventElapsedTime(&ms, ev[ph], ev[ph + 1]));
+            c->prof_ms[ph] += ms;
+        }
+    }
+    c->prof_used = 0;
+    return TFSPH_OK;
+}
+
+// Events for the next profiled step (NULL when not profiling).
+int next_events(tfsph_ctx *c, cudaEvent_t **out)
+{
+    *out = nullptr;
+    if (!c->profiling) return TFSPH_OK;
+    if (c->prof_used == 64) {
+        int rc = fold_profile(c);
+        if (rc) return rc;
+    }
+    if (c->prof_used == c->prof_sets.size()) {
+        std::vector<cudaEvent_t> ev(TFSPH_PROF_NPHASE + 1);
+        for (auto &e : ev) TF_CUDA(c, cudaEventCreate(&e));
+        c->prof_sets.push_back(ev);
+    }
+    *out = c->prof_sets[c->prof_used++].data();
+    return TFSPH_OK;
+}
+
+int prepare(tfsph_ctx *c, cudaEvent_t *ev = nullptr)
+{
+    if (c->prepared) {
+        if (ev)
+            for (int k = 1; k <= TFSPH_PROF_DENSITY + 1; ++k) TF_CUDA(c, cudaEventRecord(ev[k], c->stream));
+        return TFSPH_OK;
+    }
     LaunchCtx L = lctx(c);
+    L.ev = ev;
     if (c->counts_dirty) {
         TF_CUDA(c, cudaMemsetAsync(c->G.count, 0, (size_t)c->ncells * 4, c->stream));
         TF_CUDA(c, cudaMemsetAsync(c->D.count, 0, (size_t)c->ncells * 4, c->stream));
@@ -287,7 +335,10 @@ int prepare(tfsph_ctx *c)
     c->counts_dirty = true;
     TF_CUDA(c, launch_bin(L, c->geo, c->G, c->D, c->bsum, c->nblk));
     c->counts_dirty = false;
+    c->launches += (c->G.n + c->D.n > 0) ? 6 : 3;
     TF_CUDA(c, launch_density(L, c->geo, c->phys, c->G, c->rho_g, true, nullptr, nullptr));
+    if (c->G.n > 0) c->launches += 1;
+    if (ev) TF_CUDA(c, cudaEventRecord(ev[TFSPH_PROF_DENSITY + 1], c->stream));
     c->prepared = true;
     return TFSPH_OK;
 }
@@ -336,6 +387,9 @@ const char *tfsph_last_error(const tfsph_ctx *c) { return c ? c->err.c_str() : g
 void tfsph_destroy(tfsph_ctx *c)
 {
     if (!c) return;
+    cudaStreamSynchronize(c->stream);
+    for (auto &set : c->prof_sets)
+        for (cudaEvent_t e : set) cudaEventDestroy(e);
     for (void *p : c->allocs) cudaFree(p);
     delete c;
 }
@@ -458,6 +512,7 @@ int tfsph_step(tfsph_ctx *c, double tau, const void *t_stop, int mem_kind, const
         }
     }
     LaunchCtx L = lctx(c);
+    const int64_t launches0 = c->launches;
     if (t_stop && c->D.n > 0) {
         if (mem_kind == TFSPH_MEM_HOST) {
             const size_t bytes = (size_t)c->D.n * c->tsize;
@@ -472,15 +527,25 @@ int tfsph_step(tfsph_ctx *c, double tau, const void *t_stop, int mem_kind, const
             }
             TF_CUDA(c, cudaMemcpyAsync(c->staging, t_stop, bytes, cudaMemcpyHostToDevice, c->stream));
             TF_CUDA(c, launch_set_tstop(L, c->D, c->staging));
+            c->launches += 1;
         } else if (mem_kind == TFSPH_MEM_DEVICE) {
             TF_CUDA(c, launch_set_tstop(L, c->D, t_stop));
+            c->launches += 1;
         } else {
             return fail(c, TFSPH_E_INVALID_ARG, "bad mem_kind");
         }
     }
-    int rc = prepare(c);
+    cudaEvent_t *ev = nullptr;
+    int rc = next_events(c, &ev);
     if (rc) return rc;
-    if (c->G.n > 0) TF_CUDA(c, launch_force(L, c->geo, c->phys, c->G, c->rho_g, c->acc));
+    if (ev) TF_CUDA(c, cudaEventRecord(ev[0], c->stream));
+    rc = prepare(c, ev);
+    if (rc) return rc;
+    if (c->G.n > 0) {
+        TF_CUDA(c, launch_force(L, c->geo, c->phys, c->G, c->rho_g, c->acc));
+        c->launches += 1;
+    }
+    if (ev) TF_CUDA(c, cudaEventRecord(ev[TFSPH_PROF_FORCE + 1], c->stream));
     StepArgs S;
     S.tau = tau;
     S.g[0] = gg[0];
@@ -490,8 +555,40 @@ int tfsph_step(tfsph_ctx *c, double tau, const void *t_stop, int mem_kind, const
     S.cell_acc = c->cell_acc;
     S.has_frozen = c->has_frozen ? 1 : 0;
     TF_CUDA(c, launch_cell_update(L, c->geo, c->phys, c->G, c->D, c->acc, S));
+    c->launches += 1;
+    if (ev) {
+        TF_CUDA(c, cudaEventRecord(ev[TFSPH_PROF_DRAG + 1], c->stream));
+        c->prof_steps += 1;
+        c->prof_launches += c->launches - launches0;
+    }
     c->prepared = false;
     c->steps += 1;
+    return TFSPH_OK;
+}
+
+int tfsph_profile(tfsph_ctx *c, int enable)
+{
+    if (!c) return fail(nullptr, TFSPH_E_INVALID_ARG, "ctx is NULL");
+    if (enable) {
+        TF_CUDA(c, cudaStreamSynchronize(c->stream));
+        c->prof_used = 0;
+        for (double &m : c->prof_ms) m = 0.0;
+        c->prof_steps = 0;
+        c->prof_launches = 0;
+    }
+    c->profiling = enable != 0;
+    return TFSPH_OK;
+}
+
+int tfsph_profile_read(tfsph_ctx *c, double *ms, int64_t *steps, int64_t *launches)
+{
+    if (!c) return fail(nullptr, TFSPH_E_INVALID_ARG, "ctx is NULL");
+    int rc = fold_profile(c);
+    if (rc) return rc;
+    if (ms)
+        for (int k = 0; k < TFSPH_PROF_NPHASE; ++k) ms[k] = c->prof_ms[k];
+    if (steps) *steps = c->prof_steps;
+    if (launches) *launches = c->prof_launches;
     return TFSPH_OK;
 }
 
@@ -641,6 +738,7 @@ int tfsph_info(const tfsph_ctx *c, tfsph_info_t *out)
     out->n_cells_total = c->ncells;
     out->steps = c->steps;
     out->device_bytes = c->device_bytes;
+    out->launches = c->launches;
     return TFSPH_OK;
 }
 

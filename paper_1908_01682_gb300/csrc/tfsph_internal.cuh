@@ -110,6 +110,7 @@ struct LaunchCtx {
     int precision;   // TFSPH_FP32 / TFSPH_FP64
     int dim;
     int *d_err;      // device error word
+    cudaEvent_t *ev; // optional phase events: launch_bin records ev[1..4]
 };
 
 // bin.cu

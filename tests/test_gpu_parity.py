@@ -1,10 +1,19 @@
 """GPU path against the FP64 oracle, element by element, on seeded inputs.
 
 Bit-exact: cell keys, the (cell key, id) sort order, cell ranges, and the
-neighbour sets (count and fingerprint per particle). Within tolerance after
-one step: gas density, pressure acceleration, velocities, positions and
-energy. Tolerances (normwise ||x - x_ref|| / ||x_ref||): 1e-5 for the FP32
-path and 1e-12 for the FP64 path on density and velocities.
+neighbour sets (count and fingerprint per particle).
+
+Within tolerance after one step, tol = 1e-5 (FP32 path) or 1e-12 (FP64 path):
+- densities, positions and energies: normwise ||x - x_ref|| / ||x_ref|| <= tol
+  (the density sums have positive terms only);
+- pressure acceleration and velocities, element by element:
+      |A - A_ref|  <= tol |A_ref| + K u S_a
+      |v' - v'_ref| <= tol (|v'_ref| + |v|) + K u tau (S_a + S_cell)
+  where S_a is the magnitude sum of particle a's pair terms (reported by the
+  oracle), S_cell its mean over the cell's gas, u the unit roundoff of the
+  path (2^-24 or 2^-53) and K = 128. The pressure force of a nearly uniform
+  state is a small residual of large pair terms; rounding each term in the
+  path's precision bounds its accuracy by u S_a, whatever the order of the sum.
 """
 import math
 
@@ -17,6 +26,8 @@ from conftest import gpu_context, gpu_lib, gpu_one_step, normwise, oracle_params
 pytestmark = pytest.mark.gpu
 
 TOL = {0: 1e-5, 1: 1e-12}
+UNIT = {0: 2.0 ** -24, 1: 2.0 ** -53}
+KAPPA = 128.0
 
 
 def _oracle_step(orc, w, tau=None, g=None, **pover):
@@ -30,16 +41,35 @@ def _oracle_step(orc, w, tau=None, g=None, **pover):
 def _pos_err(a, ref, w):
     """Normwise position error with periodic differences taken as minimum images."""
     d = np.asarray(a) - np.asarray(ref)
+    if d.size == 0:
+        return 0.0
     for k in range(w.dim):
         if w.params["periodic"][k]:
             L = w.params["hi"][k] - w.params["lo"][k]
             d[k] -= L * np.round(d[k] / L)
-    return float(np.linalg.norm(d)) / float(np.linalg.norm(ref))
+    return float(np.linalg.norm(d)) / max(float(np.linalg.norm(ref)), 1e-300)
 
 
-def _compare(orc, w, tol=None, acc_floor=0.0, **over):
+def _cell_mean(values, keys, ncells, mask=None):
+    """Mean of per-particle values over each cell (0 for empty cells)."""
+    m = np.ones_like(values, dtype=bool) if mask is None else mask
+    s = np.bincount(keys[m], weights=values[m], minlength=ncells)
+    n = np.bincount(keys[m], minlength=ncells)
+    return np.where(n > 0, s / np.maximum(n, 1), 0.0)
+
+
+def _bound_ratio(err, bound):
+    """max over elements of |err| / bound (<= 1 passes)."""
+    err = np.abs(np.asarray(err, np.float64))
+    if err.size == 0:
+        return 0.0
+    return float(np.max(err / np.maximum(bound, 1e-300)))
+
+
+def _compare(orc, w, tol=None, **over):
     prec = int(over.get("precision", w.params["precision"]))
     tol = TOL[prec] if tol is None else tol
+    ku = KAPPA * UNIT[prec]
     gpu = gpu_one_step(w, **over)
     p, s, r, rho_d = _oracle_step(orc, w)
     # --- bit-exact integer results ---
@@ -52,12 +82,14 @@ def _compare(orc, w, tol=None, acc_floor=0.0, **over):
     assert np.array_equal(gpu["nb_count"], r.nb_count[r.perm_g]), "neighbour counts"
     assert np.array_equal(gpu["nb_fprint"], r.nb_fprint[r.perm_g]), "neighbour sets"
     # --- floating point after one step ---
+    tau = w.tau
+    ncells = len(r.cstart_g) - 1
+    moving = np.ones(w.n_gas, bool) if w.frozen is None else w.frozen == 0
+    S = r.acc_scale_g
+    S_cell_g = _cell_mean(S, r.keys_g, ncells, moving)
     errs = {
         "rho_g": normwise(gpu["rho_g"], r.rho_g),
         "rho_d": normwise(gpu["rho_d"], rho_d),
-        "acc_g": normwise(gpu["acc_g"], r.acc_g, floor=acc_floor),
-        "gv": normwise(gpu["gv"], s.gv),
-        "du": normwise(gpu["du"], s.du),
         "gx": _pos_err(gpu["gx"], s.gx, w),
         "dx": _pos_err(gpu["dx"], s.dx, w),
     }
@@ -65,6 +97,19 @@ def _compare(orc, w, tol=None, acc_floor=0.0, **over):
         errs["ge"] = normwise(gpu["ge"], s.ge)
     for k, e in errs.items():
         assert e <= tol, f"{k}: normwise error {e:.3e} > {tol:.0e} ({errs})"
+    ratios = {
+        "acc_g": _bound_ratio(gpu["acc_g"][:, moving] - r.acc_g[:, moving],
+                              tol * np.abs(r.acc_g[:, moving]) + ku * S[moving]),
+        "gv": _bound_ratio(gpu["gv"][:, moving] - s.gv[:, moving],
+                           tol * (np.abs(s.gv[:, moving]) + np.abs(w.gv[:, moving]))
+                           + ku * tau * (S[moving] + S_cell_g[r.keys_g][moving])),
+        "du": _bound_ratio(gpu["du"] - s.du,
+                           tol * (np.abs(s.du) + np.abs(w.du)) + ku * tau * S_cell_g[r.keys_d]),
+    }
+    for k, e in ratios.items():
+        assert e <= 1.0, f"{k}: error / bound = {e:.3e} ({ratios}; normwise {errs})"
+    errs["gv_normwise"] = normwise(gpu["gv"], s.gv)
+    errs["du_normwise"] = normwise(gpu["du"], s.du)
     return gpu, r, errs
 
 
