@@ -140,7 +140,8 @@ static int64_t orc_key(const orc_params *P, const int32_t nc[3], const double x[
 }
 
 /* ------------------------------------------------------------------------ */
-/* Pair geometry. Membership r^2 < (2h)^2 decided in the path's precision.   */
+/* Pair geometry. Membership r^2 < (2h)^2 decided in the path's precision,  */
+/* with r^2 = fma(dz, dz, fma(dy, dy, dx * dx)) (one rounding per term).     */
 /* d[] receives x_a - x_b (minimum image on periodic axes) in binary64.      */
 /*                                                                          */
 /* The decision's displacement along an axis is s = x_a - x_b; when |s|     */
@@ -183,8 +184,7 @@ static int orc_pair(const orc_params *P, const double xa[3], const double xb[3],
             float L = (float)(P->hi[k] - P->lo[k]);
             float half = (float)(0.5 * (P->hi[k] - P->lo[k]));
             float dx = orc_disp32((float)xa[k], (float)xb[k], P->periodic[k], L, half);
-            float sq = dx * dx;
-            acc = (k == 0) ? sq : acc + sq;
+            acc = (k == 0) ? dx * dx : fmaf(dx, dx, acc);
         }
         float lim = (float)(4.0 * P->h * P->h);
         inside = acc < lim;
@@ -194,8 +194,7 @@ static int orc_pair(const orc_params *P, const double xa[3], const double xb[3],
             double L = P->hi[k] - P->lo[k];
             double half = 0.5 * (P->hi[k] - P->lo[k]);
             double dx = orc_disp64(xa[k], xb[k], P->periodic[k], L, half);
-            double sq = dx * dx;
-            acc = (k == 0) ? sq : acc + sq;
+            acc = (k == 0) ? dx * dx : fma(dx, dx, acc);
         }
         inside = acc < 4.0 * P->h * P->h;
     }

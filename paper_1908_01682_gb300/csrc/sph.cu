@@ -17,6 +17,7 @@
 // operations so that it is a plain IEEE decision, the same one the checker
 // takes.
 #include <algorithm>
+#include <cmath>
 
 #include "tfsph_internal.cuh"
 
@@ -69,13 +70,13 @@ __device__ __forceinline__ T pair_r2(const Geo<T> &G, const V4<T> &pa, const V4<
     T r2 = mul_rn(d[0], d[0]);
     if (DIM > 1) {
         d[1] = SEAM ? disp(pa.y, pb.y, G.per[1], G.L[1], G.halfL[1]) : sub_rn(pa.y, pb.y);
-        r2 = add_rn(r2, mul_rn(d[1], d[1]));
+        r2 = fma_rn(d[1], d[1], r2);
     } else {
         d[1] = T(0);
     }
     if (DIM > 2) {
         d[2] = SEAM ? disp(pa.z, pb.z, G.per[2], G.L[2], G.halfL[2]) : sub_rn(pa.z, pb.z);
-        r2 = add_rn(r2, mul_rn(d[2], d[2]));
+        r2 = fma_rn(d[2], d[2], r2);
     } else {
         d[2] = T(0);
     }
@@ -104,24 +105,26 @@ template <class T, int MODE> struct PairAcc {
     {
         if (!(r2 < G.h2x4)) return;
         if (MODE <= 1) {
-            sum += kernel_w(G, sqrt(r2) * G.inv_h);
+            sum += kernel_w(G, approx_sqrt(r2) * G.inv_h);
             if (MODE == 1) {
                 ++cnt;
                 fp += (uint64_t)((idb & kIdMask) + 1u) * 0x9E3779B97F4A7C15ull;
             }
         } else {
-            const T F = kernel_f(G, sqrt(r2) * G.inv_h);  // (1/r) dW/dr
+            if (r2 == T(0)) return;  // self or coincident particle: zero gradient
+            const T inv_r = approx_rsqrt(r2);
+            const T F = kernel_f(G, r2 * inv_r * G.inv_h, G.h * inv_r);  // (1/r) dW/dr
             T coef = qa + pb.w;
             if (MODE == 3) {
                 const T vx = va.x - vb->x, vy = va.y - vb->y, vz = va.z - vb->z;
                 const T vr = vx * d[0] + vy * d[1] + vz * d[2];
                 T pi = T(0);
                 if (Ph.av && vr < T(0)) {
-                    const T mu = Ph.h * vr / (r2 + Ph.eta2);
-                    const T cb = Ph.eos == TFSPH_EOS_ADIABATIC ? sqrt(Ph.gamma * Ph.gm1 * vb->w) : Ph.cs;
+                    const T mu = approx_div(Ph.h * vr, r2 + Ph.eta2);
+                    const T cb = Ph.eos == TFSPH_EOS_ADIABATIC ? approx_sqrt(Ph.gamma * Ph.gm1 * vb->w) : Ph.cs;
                     const T cbar = T(0.5) * (ca + cb);
                     const T rbar = T(0.5) * (rhoa + rhob);
-                    pi = (-Ph.av_alpha * cbar * mu + Ph.av_beta * mu * mu) / rbar;
+                    pi = approx_div(-Ph.av_alpha * cbar * mu + Ph.av_beta * mu * mu, rbar);
                 }
                 coef += pi;
                 de += (qa + T(0.5) * pi) * vr * F;
@@ -346,7 +349,25 @@ struct TileCfg {
     int nrows;    // T1 T2 owned rows
     int cap;      // particles that fit in shared memory
     int offset;   // byte offset of the particle arrays in shared memory
+    float invH[2];  // 1 / H0, 1 / H1
 };
+
+// q = floor(x / d) for 0 <= x < 2^22 and 0 < d < 2^10 by a float multiply with
+// the rounded reciprocal: (x + 1/2)/d lies at least 1/(2d) from an integer,
+// more than the product's rounding error, so the truncation is exact.
+__device__ __forceinline__ int small_div(int x, int d, float inv_d)
+{
+    return (int)(((float)x + 0.5f) * inv_d);
+}
+
+// Halo cell h -> (hx, hy, hz), without integer division.
+__device__ __forceinline__ void halo_coords(int h, const TileCfg &C, int &hx, int &hy, int &hz)
+{
+    const int row = small_div(h, C.H[0], C.invH[0]);
+    hx = h - row * C.H[0];
+    hz = small_div(row, C.H[1], C.invH[1]);
+    hy = row - hz * C.H[1];
+}
 
 // In-place exclusive scan of m values in shared memory by the whole block;
 // a[m] receives the total.
@@ -461,7 +482,7 @@ __device__ __forceinline__ void walk_tile(PairAcc<T, MODE> &A, const Geo<T> &G, 
             }
             // x window: the cells whose slab lies within t = sqrt(rem)/w of the
             // particle, (o - fx) <= t for o > 0 and (fx + |o| - 1) <= t for o < 0
-            const T t = sqrt(G.lim2 - dz2 - dy2) * G.inv_w[0];
+            const T t = approx_sqrt(G.lim2 - dz2 - dy2) * G.inv_w[0];
             const int ohi = min(G.R[0], max(0, (int)floor(fx + t)));
             const int olo = -min(G.R[0], max(0, (int)floor(t - fx + T(1))));
             const int hrow = C.H[0] * ((hy + oy) + C.H[1] * (hz + oz));
@@ -534,7 +555,8 @@ k_pair_tile(Geo<T> G, Phys<T> Ph, TileCfg C, const V4<T> *__restrict__ pos, cons
     // halo cell counts; a ragged tile needs only ext + 2R halo cells per axis,
     // which keeps every raw coordinate within (-n, 2n) so one wrap suffices
     for (int h = tid; h < C.nhalo; h += blockDim.x) {
-        const int hx = h % C.H[0], hy = (h / C.H[0]) % C.H[1], hz = h / (C.H[0] * C.H[1]);
+        int hx, hy, hz;
+        halo_coords(h, C, hx, hy, hz);
         const bool inside = hx < ext[0] + 2 * G.R[0] && hy < ext[1] + 2 * G.R[1] && hz < ext[2] + 2 * G.R[2];
         const int gx = inside ? halo_cell(G, 0, c0[0], hx) : -1;
         const int gy = DIM > 1 ? halo_cell(G, 1, c0[1], hy) : 0;
@@ -557,7 +579,8 @@ k_pair_tile(Geo<T> G, Phys<T> Ph, TileCfg C, const V4<T> *__restrict__ pos, cons
         for (int h = tid; h < C.nhalo; h += blockDim.x) {
             const int j0 = lstart[h], j1 = lstart[h + 1];
             if (j1 == j0) continue;
-            const int hx = h % C.H[0], hy = (h / C.H[0]) % C.H[1], hz = h / (C.H[0] * C.H[1]);
+            int hx, hy, hz;
+            halo_coords(h, C, hx, hy, hz);
             const int gx = halo_cell(G, 0, c0[0], hx);
             const int gy = DIM > 1 ? halo_cell(G, 1, c0[1], hy) : 0;
             const int gz = DIM > 2 ? halo_cell(G, 2, c0[2], hz) : 0;
@@ -611,19 +634,23 @@ template <class T, int MODE> constexpr int tile_bytes_per_particle()
                      : (MODE == 1 ? (int)(sizeof(V4<T>) + 4) : (int)sizeof(V4<T>));
 }
 
-// Tile shape for a phase with `mean` particles per cell: the largest box
-// (halved along its longest axis) whose expected halo fills at most 80 % of
-// the shared-memory capacity. Returns false when an axis wraps fully.
+// Tile shape for a phase with `mean` particles per cell. Each CTA thread
+// takes one owned particle, so a tile is sized to hold about 7/8 of the
+// block's threads on average (a tile holding more than one particle per
+// thread runs a second, mostly idle pass); its halo must fill at most 80 %
+// of the shared-memory capacity. Returns false when an axis wraps fully.
 template <class T>
 bool plan_tiles(const Geo<T> &G, int dim, double mean, int bytes_pp, int smem_budget, TileCfg &C, size_t &smem)
 {
     for (int k = 0; k < dim; ++k)
         if (G.full[k]) return false;
+    const double target_cells = std::max(1.0, 0.875 * kTileThreads / std::max(mean, 1e-6));
+    const int side = std::max(1, (int)std::floor(std::pow(target_cells, 1.0 / dim) + 1e-9));
     int Tt[3] = {1, 1, 1};
-    if (dim == 1) Tt[0] = 1024;
-    else if (dim == 2) Tt[0] = Tt[1] = 32;
-    else Tt[0] = Tt[1] = Tt[2] = 8;
-    for (int k = 0; k < dim; ++k) Tt[k] = std::max(1, std::min(Tt[k], G.n[k]));
+    for (int k = 1; k < dim; ++k) Tt[k] = std::min(side, G.n[k]);
+    double rest = 1.0;
+    for (int k = 1; k < dim; ++k) rest *= Tt[k];
+    Tt[0] = std::max(1, std::min(G.n[0], (int)std::floor(target_cells / rest + 1e-9)));
     for (;;) {
         int H[3] = {1, 1, 1};
         long nh = 1;
@@ -640,7 +667,7 @@ bool plan_tiles(const Geo<T> &G, int dim, double mean, int bytes_pp, int smem_bu
         for (int k = 1; k < dim; ++k)
             if (Tt[k] > Tt[kmax]) kmax = k;
         if ((cap > 0 && expected <= 0.8 * (double)cap) || Tt[kmax] == 1) {
-            if (cap <= 0) return false;
+            if (cap <= 0 || nh >= (1L << 22) || H[0] >= 1024 || H[1] >= 1024) return false;
             for (int k = 0; k < 3; ++k) {
                 C.T[k] = Tt[k];
                 C.H[k] = H[k];
@@ -648,6 +675,8 @@ bool plan_tiles(const Geo<T> &G, int dim, double mean, int bytes_pp, int smem_bu
             }
             C.nhalo = (int)nh;
             C.nrows = (int)nrows;
+            C.invH[0] = 1.0f / (float)H[0];
+            C.invH[1] = 1.0f / (float)H[1];
             C.cap = (int)cap;
             C.offset = (int)offset;
             smem = (size_t)offset + (size_t)cap * (size_t)bytes_pp;

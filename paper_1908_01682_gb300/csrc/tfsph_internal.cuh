@@ -190,25 +190,45 @@ template <class T> __device__ __forceinline__ T wrap_periodic(T x, T lo, T L)
     return r;
 }
 
-// M4 cubic spline (support 2h): W = wnorm * w(q), (1/r) dW/dr = fnorm * f(q).
+// Value arithmetic (never a decision): hardware approximations in binary32
+// (sqrt.approx / rsqrt.approx, relative error below 2^-22; fast division,
+// 2 ulp), IEEE operations in binary64.
+__device__ __forceinline__ float approx_sqrt(float x)
+{
+    float r;
+    asm("sqrt.approx.f32 %0, %1;" : "=f"(r) : "f"(x));
+    return r;
+}
+__device__ __forceinline__ double approx_sqrt(double x) { return sqrt(x); }
+__device__ __forceinline__ float approx_rsqrt(float x)
+{
+    float r;
+    asm("rsqrt.approx.f32 %0, %1;" : "=f"(r) : "f"(x));
+    return r;
+}
+__device__ __forceinline__ double approx_rsqrt(double x) { return 1.0 / sqrt(x); }
+__device__ __forceinline__ float approx_div(float a, float b) { return __fdividef(a, b); }
+__device__ __forceinline__ double approx_div(double a, double b) { return a / b; }
+
+// Fused multiply-add with one rounding, for the neighbour decision r^2.
+__device__ __forceinline__ float fma_rn(float a, float b, float c) { return __fmaf_rn(a, b, c); }
+__device__ __forceinline__ double fma_rn(double a, double b, double c) { return __fma_rn(a, b, c); }
+
+// M4 cubic spline (support 2h), branch free on q in [0, 2):
+//   W = wnorm * (q < 1 ? 1 - 3/2 q^2 + 3/4 q^3 : 1/4 (2 - q)^3)
+//   (1/r) dW/dr = fnorm * (q < 1 ? -3 + 9/4 q : -3/4 (2 - q)^2 / q)
 template <class T> __device__ __forceinline__ T kernel_w(const Geo<T> &G, T q)
 {
-    if (q < T(1)) return G.wnorm * (T(1) - T(1.5) * q * q + T(0.75) * q * q * q);
-    if (q < T(2)) {
-        T a = T(2) - q;
-        return G.wnorm * T(0.25) * a * a * a;
-    }
-    return T(0);
+    const T a = fmax(T(2) - q, T(0));
+    const T inner = T(1) + q * q * (T(-1.5) + T(0.75) * q);
+    const T outer = T(0.25) * a * a * a;
+    return G.wnorm * (q < T(1) ? inner : outer);
 }
 
-template <class T> __device__ __forceinline__ T kernel_f(const Geo<T> &G, T q)
+template <class T> __device__ __forceinline__ T kernel_f(const Geo<T> &G, T q, T inv_q)
 {
-    if (q < T(1)) return G.fnorm * (T(-3) + T(2.25) * q);
-    if (q < T(2)) {
-        T a = T(2) - q;
-        return G.fnorm * (T(-0.75) * a * a / q);
-    }
-    return T(0);
+    const T a = fmax(T(2) - q, T(0));
+    return G.fnorm * (q < T(1) ? T(-3) + T(2.25) * q : T(-0.75) * a * a * inv_q);
 }
 
 }  // namespace tfsph
