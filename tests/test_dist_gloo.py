@@ -1,0 +1,57 @@
+"""Host-side multi-rank logic of bench.py on CPU (gloo, world size 2).
+
+Each rank runs an independent replica (the step has no data-path collective);
+the timing is the maximum over ranks and the value sums every rank's units.
+"""
+import os
+import socket
+
+import pytest
+
+torch = pytest.importorskip("torch")
+import torch.multiprocessing as mp  # noqa: E402
+
+
+def _free_port():
+    with socket.socket() as s:
+        s.bind(("127.0.0.1", 0))
+        return s.getsockname()[1]
+
+
+def _worker(rank, world, port, q):
+    os.environ.update(RANK=str(rank), WORLD_SIZE=str(world), LOCAL_RANK=str(rank),
+                      MASTER_ADDR="127.0.0.1", MASTER_PORT=str(port))
+    import bench
+    d = bench.Dist()
+    d.init("gloo")
+    try:
+        d.barrier()
+        t = d.max(1.0 + rank)             # per-rank timed region
+        units = d.sum(1000.0 * (rank + 1))  # per-rank particle updates
+        q.put((rank, t, units, d.world))
+    finally:
+        d.close()
+
+
+def test_bench_dist_gloo_two_ranks():
+    ctx = mp.get_context("spawn")
+    q = ctx.Queue()
+    port = _free_port()
+    procs = [ctx.Process(target=_worker, args=(r, 2, port, q)) for r in range(2)]
+    for p in procs:
+        p.start()
+    out = sorted(q.get(timeout=120) for _ in procs)
+    for p in procs:
+        p.join(timeout=60)
+        assert p.exitcode == 0
+    assert [o[1] for o in out] == [2.0, 2.0]          # max over ranks
+    assert [o[2] for o in out] == [3000.0, 3000.0]    # whole-job units
+    assert all(o[3] == 2 for o in out)
+
+
+def test_reference_arm_other_ranks_exit_without_work(capsys, monkeypatch):
+    import bench
+    monkeypatch.setenv("RANK", "1")
+    monkeypatch.setenv("WORLD_SIZE", "2")
+    bench.main(["--impl", "reference", "--steps", "1", "--warmup", "0"])
+    assert capsys.readouterr().out == ""
