@@ -208,6 +208,29 @@ void tfsph_destroy(tfsph_ctx *c);
 /* Library version, major * 10000 + minor * 100 + patch. */
 int tfsph_version(void);
 
+/* Cell ranges of a set of cell keys, computed without allocating any device
+ * memory. The paper has no counterpart: this is an entry point for callers
+ * that cannot call cudaMalloc, such as applications whose device memory is
+ * handed out by their own fixed pool, or loops that must not allocate (or
+ * pay the device synchronisation an allocation can bring) once running.
+ *   keys:   n device cell keys (uint32); keys >= n_cells are not counted.
+ *   starts: n_cells + 1 device values (caller-owned). starts[c] is the
+ *           number of counted keys below c, starts[n_cells] the number of
+ *           counted keys; keys sorted ascending make [starts[c],
+ *           starts[c+1]) the slots of cell c.
+ *   stream: cudaStream_t (NULL = legacy default stream); asynchronous.
+ * The scratch (2^21 cell counters and the scan's block totals, 8 MiB in all)
+ * is one static device array that every GPU loading the library holds until
+ * the process exits; n_cells above 2^21 is rejected with INVALID_ARG. The
+ * first call on a device looks up that array's device address (with the
+ * device current); make that first call before any stream capture. All calls
+ * on a device share that device's array and each clears the counters it
+ * uses first, so calls that overlap on the same GPU (on different streams)
+ * race: order them on one stream. Errors: INVALID_ARG, CUDA; the message is
+ * in tfsph_last_error(NULL). */
+int tfsph_cell_ranges_noalloc(const uint32_t *keys, int64_t n, uint32_t n_cells, uint32_t *starts,
+                              void *stream);
+
 #ifdef __cplusplus
 }
 #endif

@@ -92,6 +92,7 @@ def load() -> C.CDLL:
     lib.tfsph_info.argtypes = [ctxp, C.POINTER(tfsph_info_t)]
     lib.tfsph_sync.argtypes = [ctxp]
     lib.tfsph_profile.argtypes = [ctxp, i32]
+    lib.tfsph_cell_ranges_noalloc.argtypes = [vp, i64, C.c_uint32, vp, vp]
     lib.tfsph_profile_read.argtypes = [ctxp, vp, vp, vp]
     lib.tfsph_last_error.argtypes = [ctxp]
     lib.tfsph_last_error.restype = C.c_char_p
@@ -102,7 +103,7 @@ def load() -> C.CDLL:
     lib.tfsph_version.argtypes = []
     for name in ("tfsph_init", "tfsph_set_state", "tfsph_set_stream", "tfsph_step", "tfsph_max_dt",
                  "tfsph_fields", "tfsph_debug", "tfsph_info", "tfsph_sync", "tfsph_version",
-                 "tfsph_profile", "tfsph_profile_read"):
+                 "tfsph_profile", "tfsph_profile_read", "tfsph_cell_ranges_noalloc"):
         getattr(lib, name).restype = C.c_int
     _lib = lib
     return lib
@@ -173,6 +174,11 @@ def tfsph_profile_read(ctx):
     rc = load().tfsph_profile_read(ctx, C.cast(ms, C.c_void_p), C.cast(C.pointer(steps), C.c_void_p),
                                    C.cast(C.pointer(launches), C.c_void_p))
     return rc, np.array(ms[:], dtype=np.float64), steps.value, launches.value
+
+
+def tfsph_cell_ranges_noalloc(keys_ptr, n: int, n_cells: int, starts_ptr, stream_ptr=None) -> int:
+    """Cell ranges of device keys into device starts, using only static scratch."""
+    return load().tfsph_cell_ranges_noalloc(keys_ptr, int(n), int(n_cells), starts_ptr, stream_ptr)
 
 
 def tfsph_last_error(ctx) -> str:

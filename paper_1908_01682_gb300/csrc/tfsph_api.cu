@@ -364,6 +364,8 @@ int emit(tfsph_ctx *c, const void *src, size_t bytes, void *out, int mem_kind)
 
 }  // namespace
 
+void tfsph::set_unbound_error(const char *msg) { g_init_error = msg; }
+
 extern "C" {
 
 int tfsph_version(void) { return 10000; }

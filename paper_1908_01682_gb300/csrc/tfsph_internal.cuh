@@ -134,6 +134,9 @@ cudaError_t launch_density(const LaunchCtx &L, const void *geo, const void *phys
 cudaError_t launch_force(const LaunchCtx &L, const void *geo, const void *phys, PhaseBufs &G,
                          const void *rho, void *acc);
 
+// tfsph_api.cu: message for tfsph_last_error(NULL) from calls without a context
+void set_unbound_error(const char *msg);
+
 // drag.cu
 struct StepArgs {
     double tau;
