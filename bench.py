@@ -212,6 +212,36 @@ def peaks():
         return {"hbm_gbs": 6800.0, "sm_max_mhz": 2070.0}, "fallback"
 
 
+PHASE_SOURCE = {"count": "bin.cu", "scan": "bin.cu", "scatter": "bin.cu", "gather": "bin.cu",
+                "density": "sph.cu", "force": "sph.cu", "drag": "drag.cu"}
+
+
+def kernel_source_hash(phase: str) -> str:
+    """sha256 of the phase's kernel source and the shared internal header."""
+    import hashlib
+    csrc = os.path.join(ROOT, "paper_1908_01682_gb300", "csrc")
+    hsh = hashlib.sha256()
+    for f in (PHASE_SOURCE[phase], "tfsph_internal.cuh"):
+        with open(os.path.join(csrc, f), "rb") as fh:
+            hsh.update(fh.read())
+    return hsh.hexdigest()
+
+
+def recorded_traffic(workload: str, phase: str):
+    """DRAM bytes (read + write) per launch of the phase's kernel from the
+    committed ncu summary, or None when absent or taken on other source."""
+    path = os.path.join(ROOT, "profiles", "traffic.json")
+    try:
+        with open(path) as f:
+            rec = json.load(f)
+        ent = rec[workload][phase]
+    except (OSError, ValueError, KeyError):
+        return None
+    if ent.get("source_sha256") != kernel_source_hash(phase):
+        return None
+    return float(ent["dram_bytes_per_launch"])
+
+
 def fp32_alu_peak_tflops(sm_count: int, mhz: float) -> float:
     """FP32 FMA pipes: 128 lanes per SM, 2 flops per FMA."""
     return sm_count * 128 * 2 * mhz * 1e6 / 1e12
@@ -351,7 +381,7 @@ def run_ours(args, dist: Dist):
     step_bytes = sum(algorithmic(ph, w, info, nb_mean)[1] for ph in ("count", "scan", "scatter", "gather", "drag")) \
         + (24.0 + 32.0) * w.n_gas
     roof = {"kernel": dominant, "bound": bound, "achieved": achieved, "peak": peak, "unit": unit,
-            "frac": achieved / peak, "traffic": None,
+            "frac": achieved / peak, "traffic": recorded_traffic(args.workload, dominant),
             "peak_source": f"{pk_src}" + ("" if bound == "hbm" else f" (FP32 FMA lanes x {sm_count} SMs x SM clock)"),
             "step_hbm_frac": (step_bytes / (ms_per_step * 1e-3) / 1e9) / float(pk.get("hbm_gbs", 6800.0)),
             "step_algorithmic_bytes": step_bytes}
