@@ -167,6 +167,25 @@ int tfsph_set_stream(tfsph_ctx *c, void *stream);
  * next tfsph_sync / tfsph_fields as NONFINITE. */
 int tfsph_step(tfsph_ctx *c, double tau, const void *t_stop, int mem_kind, const double g[3]);
 
+/* Reverse-mode derivative of one tfsph_step taken from the context's current
+ * state (the state is not changed), for the isothermal gas without
+ * artificial viscosity (INVALID_ARG otherwise). It differentiates the step of
+ * Eqs. 19-21 as computed here: the implicit cell drag and particle update,
+ * the SPH pressure force and the summation density; cell membership is
+ * piecewise constant and has no derivative.
+ *   In:  lam_gx, lam_gv = dLoss/d(x', v') of the gas after the step,
+ *        lam_dx, lam_du = dLoss/d(x', u') of the dust after the step.
+ *   Out: lam_gx, lam_gv, lam_du overwritten with dLoss/d(x, v, u) before the
+ *        step (lam_dx passes through unchanged: dust positions enter the step
+ *        only through cell membership); lam_ts (n_dust) is ADDED
+ *        dLoss/dt_stop of this step.
+ * All arrays component-major in id order, of the context's precision, in
+ * memory of mem_kind (host arrays are copied and the call synchronises).
+ * Rolling out several steps: restore the state at the start of each step
+ * (tfsph_set_state) and call this in reverse order, carrying the lambdas. */
+int tfsph_step_adjoint(tfsph_ctx *c, double tau, const double g[3], void *lam_gx, void *lam_gv,
+                       void *lam_dx, void *lam_du, void *lam_ts, int mem_kind);
+
 /* Courant step (Eq. 4): *tau_out = cfl * h / max over moving gas of
  * max(|v_a|, c_a). Synchronises the stream. */
 int tfsph_max_dt(tfsph_ctx *c, double cfl, double *tau_out);

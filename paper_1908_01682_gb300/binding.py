@@ -87,6 +87,7 @@ def load() -> C.CDLL:
     lib.tfsph_set_stream.argtypes = [ctxp, vp]
     lib.tfsph_step.argtypes = [ctxp, d, vp, i32, C.POINTER(d)]
     lib.tfsph_max_dt.argtypes = [ctxp, d, C.POINTER(d)]
+    lib.tfsph_step_adjoint.argtypes = [ctxp, d, C.POINTER(d), vp, vp, vp, vp, vp, i32]
     lib.tfsph_fields.argtypes = [ctxp, i32, vp, i32, i32]
     lib.tfsph_debug.argtypes = [ctxp, i32, vp, i32]
     lib.tfsph_info.argtypes = [ctxp, C.POINTER(tfsph_info_t)]
@@ -101,7 +102,7 @@ def load() -> C.CDLL:
     lib.tfsph_destroy.argtypes = [ctxp]
     lib.tfsph_destroy.restype = None
     lib.tfsph_version.argtypes = []
-    for name in ("tfsph_init", "tfsph_set_state", "tfsph_set_stream", "tfsph_step", "tfsph_max_dt",
+    for name in ("tfsph_init", "tfsph_set_state", "tfsph_set_stream", "tfsph_step", "tfsph_step_adjoint", "tfsph_max_dt",
                  "tfsph_fields", "tfsph_debug", "tfsph_info", "tfsph_sync", "tfsph_version",
                  "tfsph_profile", "tfsph_profile_read", "tfsph_cell_ranges_noalloc"):
         getattr(lib, name).restype = C.c_int
@@ -136,6 +137,11 @@ def tfsph_set_stream(ctx, stream_ptr) -> int:
 def tfsph_step(ctx, tau: float, tstop_ptr, mem_kind: int, g) -> int:
     g3 = (C.c_double * 3)(*[float(g[k]) if k < len(g) else 0.0 for k in range(3)])
     return load().tfsph_step(ctx, float(tau), tstop_ptr, int(mem_kind), g3)
+
+
+def tfsph_step_adjoint(ctx, tau: float, g, lam_gx, lam_gv, lam_dx, lam_du, lam_ts, mem_kind: int) -> int:
+    g3 = (C.c_double * 3)(*[float(g[k]) if k < len(g) else 0.0 for k in range(3)])
+    return load().tfsph_step_adjoint(ctx, float(tau), g3, lam_gx, lam_gv, lam_dx, lam_du, lam_ts, int(mem_kind))
 
 
 def tfsph_max_dt(ctx, cfl: float):
@@ -292,6 +298,20 @@ class Context:
                 tstop = np.ascontiguousarray(tstop, dtype=self.dtype)
                 tp = tstop.ctypes.data
         _check(tfsph_step(self.ctx, tau, tp, mem, g), self.ctx)
+
+    def step_adjoint(self, tau: float, g, lam_gx, lam_gv, lam_dx, lam_du, lam_ts):
+        """Reverse-mode derivative of one step from the current state, in place
+        on the lambda arrays (numpy host arrays or torch CUDA tensors)."""
+        arrs = (lam_gx, lam_gv, lam_dx, lam_du, lam_ts)
+        if _is_torch(lam_gx):
+            ptrs = [a.data_ptr() for a in arrs]
+            mem = TFSPH_MEM_DEVICE
+        else:
+            for a in arrs:
+                assert a.dtype == self.dtype and a.flags.c_contiguous
+            ptrs = [a.ctypes.data for a in arrs]
+            mem = TFSPH_MEM_HOST
+        _check(tfsph_step_adjoint(self.ctx, tau, g, *ptrs, mem), self.ctx)
 
     def max_dt(self, cfl: float) -> float:
         rc, tau = tfsph_max_dt(self.ctx, cfl)

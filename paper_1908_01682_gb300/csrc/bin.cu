@@ -325,6 +325,62 @@ __global__ void __launch_bounds__(256) k_max_final(const T *__restrict__ partial
     if (threadIdx.x == 0) *out = red[0];
 }
 
+// Adjoint vectors: component-major id order <-> V4 storage order.
+template <class T>
+__global__ void k_lam_gather(const uint32_t *__restrict__ id, int n, int dim, const T *__restrict__ lam,
+                             V4<T> *__restrict__ out)
+{
+    const int s = blockIdx.x * blockDim.x + threadIdx.x;
+    if (s >= n) return;
+    const size_t i = id[s] & kIdMask;
+    V4<T> v;
+    v.x = lam[i];
+    v.y = dim > 1 ? lam[(size_t)n + i] : T(0);
+    v.z = dim > 2 ? lam[2 * (size_t)n + i] : T(0);
+    v.w = T(0);
+    out[s] = v;
+}
+
+template <class T>
+__global__ void k_lam_scatter(const uint32_t *__restrict__ id, int n, int dim, const V4<T> *__restrict__ a,
+                              const V4<T> *__restrict__ b, T *__restrict__ lam)
+{
+    const int s = blockIdx.x * blockDim.x + threadIdx.x;
+    if (s >= n) return;
+    const size_t i = id[s] & kIdMask;
+    V4<T> v = a[s];
+    if (b) {
+        const V4<T> w = b[s];
+        v.x += w.x;
+        v.y += w.y;
+        v.z += w.z;
+    }
+    lam[i] = v.x;
+    if (dim > 1) lam[(size_t)n + i] = v.y;
+    if (dim > 2) lam[2 * (size_t)n + i] = v.z;
+}
+
+// lambda_t (id order) += lambda_t (storage order)
+template <class T>
+__global__ void k_lam_add_scalar(const uint32_t *__restrict__ id, int n, const T *__restrict__ src,
+                                 T *__restrict__ dst)
+{
+    const int s = blockIdx.x * blockDim.x + threadIdx.x;
+    if (s >= n) return;
+    dst[id[s] & kIdMask] += src[s];
+}
+
+// lambda_rho = dq/drho lambda_q with q = cs^2 / rho (isothermal): -cs^2/rho^2 lambda_q
+template <class T>
+__global__ void k_lamq_to_lamrho(const V4<T> *__restrict__ lq, const T *__restrict__ rho, int n, T cs2,
+                                 T *__restrict__ lrho)
+{
+    const int s = blockIdx.x * blockDim.x + threadIdx.x;
+    if (s >= n) return;
+    const T r = rho[s];
+    lrho[s] = -cs2 / (r * r) * lq[s].w;
+}
+
 inline int grid_for(int64_t n, int threads) { return (int)((n + threads - 1) / threads); }
 
 template <class T>
@@ -494,6 +550,66 @@ cudaError_t launch_max_speed(const LaunchCtx &L, const void *phys, const PhaseBu
 {
     return L.precision == TFSPH_FP64 ? max_speed_t<double>(L, phys, G, partials, nblk, result)
                                      : max_speed_t<float>(L, phys, G, partials, nblk, result);
+}
+
+cudaError_t launch_lam_gather(const LaunchCtx &L, const PhaseBufs &P, const void *lam, void *out)
+{
+    if (P.n == 0) return cudaSuccess;
+    const int n = (int)P.n;
+    if (L.precision == TFSPH_FP64)
+        k_lam_gather<double><<<grid_for(n, 256), 256, 0, L.stream>>>(P.id[P.cur], n, L.dim,
+                                                                     static_cast<const double *>(lam),
+                                                                     static_cast<double4a *>(out));
+    else
+        k_lam_gather<float><<<grid_for(n, 256), 256, 0, L.stream>>>(P.id[P.cur], n, L.dim, static_cast<const float *>(lam),
+                                                                    static_cast<float4 *>(out));
+    return cudaGetLastError();
+}
+
+cudaError_t launch_lam_scatter(const LaunchCtx &L, const PhaseBufs &P, const void *a, const void *b, void *lam)
+{
+    if (P.n == 0) return cudaSuccess;
+    const int n = (int)P.n;
+    if (L.precision == TFSPH_FP64)
+        k_lam_scatter<double><<<grid_for(n, 256), 256, 0, L.stream>>>(
+            P.id[P.cur], n, L.dim, static_cast<const double4a *>(a), static_cast<const double4a *>(b),
+            static_cast<double *>(lam));
+    else
+        k_lam_scatter<float><<<grid_for(n, 256), 256, 0, L.stream>>>(P.id[P.cur], n, L.dim,
+                                                                     static_cast<const float4 *>(a),
+                                                                     static_cast<const float4 *>(b),
+                                                                     static_cast<float *>(lam));
+    return cudaGetLastError();
+}
+
+cudaError_t launch_lam_add_scalar(const LaunchCtx &L, const PhaseBufs &P, const void *src, void *dst)
+{
+    if (P.n == 0) return cudaSuccess;
+    const int n = (int)P.n;
+    if (L.precision == TFSPH_FP64)
+        k_lam_add_scalar<double><<<grid_for(n, 256), 256, 0, L.stream>>>(P.id[P.cur], n,
+                                                                         static_cast<const double *>(src),
+                                                                         static_cast<double *>(dst));
+    else
+        k_lam_add_scalar<float><<<grid_for(n, 256), 256, 0, L.stream>>>(P.id[P.cur], n, static_cast<const float *>(src),
+                                                                        static_cast<float *>(dst));
+    return cudaGetLastError();
+}
+
+cudaError_t launch_lamq_to_lamrho(const LaunchCtx &L, const PhaseBufs &P, const void *lq, const void *rho, double cs2,
+                                  void *lrho)
+{
+    if (P.n == 0) return cudaSuccess;
+    const int n = (int)P.n;
+    if (L.precision == TFSPH_FP64)
+        k_lamq_to_lamrho<double><<<grid_for(n, 256), 256, 0, L.stream>>>(static_cast<const double4a *>(lq),
+                                                                         static_cast<const double *>(rho), n, cs2,
+                                                                         static_cast<double *>(lrho));
+    else
+        k_lamq_to_lamrho<float><<<grid_for(n, 256), 256, 0, L.stream>>>(static_cast<const float4 *>(lq),
+                                                                        static_cast<const float *>(rho), n, (float)cs2,
+                                                                        static_cast<float *>(lrho));
+    return cudaGetLastError();
 }
 
 cudaError_t launch_debug_keys(const LaunchCtx &L, const void *geo, const PhaseBufs &P, uint32_t *out)

@@ -83,10 +83,28 @@ __device__ __forceinline__ T pair_r2(const Geo<T> &G, const V4<T> &pa, const V4<
     return r2;
 }
 
+// Per-candidate data staged besides the position: a second V4 (velocity for
+// the full force, lambda_A for the force adjoint) and/or one scalar (density
+// for the full force, lambda_rho for the density adjoint).
+template <int MODE> struct ModeUses {
+    static constexpr bool vel = MODE == 3 || MODE == 4;
+    static constexpr bool rho = MODE == 3 || MODE == 5;
+};
+
 // ---------------------------------------------------------------------------
 // Per-pair work. MODE 0: density, 1: density + neighbour statistics,
 // 2: isothermal force without viscosity, 3: force with viscosity and/or
-// adiabatic energy rate.
+// adiabatic energy rate, 4: adjoint of the isothermal force, 5: adjoint of
+// the density.
+//
+// Adjoints (reverse mode, lambda_X = dLoss/dX), as gathers over neighbours:
+//   A_a   = -m sum_b (q_a + q_b) F(r_ab) d_ab,  d_ab = x_a - x_b,
+//           F = (1/r) dW/dr, q = p/rho^2;
+//   lambda_q_a  = -m sum_b F_ab d_ab . (lambda_A_a - lambda_A_b)
+//   lambda_x_a += -m sum_b (q_a + q_b) M(d_ab) (lambda_A_a - lambda_A_b),
+//           M(d) v = F v + (F'(r)/r) (d . v) d
+//   rho_a = m sum_b W(r_ab):
+//   lambda_x_a += m sum_b F_ab d_ab (lambda_rho_a + lambda_rho_b)
 // ---------------------------------------------------------------------------
 template <class T, int MODE> struct PairAcc {
     // density
@@ -97,6 +115,8 @@ template <class T, int MODE> struct PairAcc {
     T qa = T(0), rhoa = T(1), ca = T(0);
     V4<T> va;
     T ax = T(0), ay = T(0), az = T(0), de = T(0);
+    // adjoints: lambda_A_a (in va), lambda_rho_a (in rhoa); lambda_q in de,
+    // lambda_x in ax, ay, az
 
     // candidate b: position (with p_b/rho_b^2 in .w), velocity, density, id,
     // squared distance r2 and displacement d = x_a - x_b
@@ -104,6 +124,29 @@ template <class T, int MODE> struct PairAcc {
                                         T rhob, uint32_t idb, T r2, const T d[3])
     {
         if (!(r2 < G.h2x4)) return;
+        if (MODE == 4 || MODE == 5) {
+            if (r2 == T(0)) return;  // zero displacement: no contribution
+            const T inv_r = approx_rsqrt(r2);
+            const T q = r2 * inv_r * G.inv_h;
+            const T inv_q = G.h * inv_r;
+            const T F = kernel_f(G, q, inv_q);
+            if (MODE == 4) {
+                const T dx = va.x - vb->x, dy = va.y - vb->y, dz = va.z - vb->z;  // lambda_A_a - lambda_A_b
+                const T dd = d[0] * dx + d[1] * dy + d[2] * dz;
+                de -= Ph.m_g * F * dd;
+                const T c = -Ph.m_g * (qa + pb.w);
+                const T Fr = kernel_fprime(G, q, inv_q) * inv_r;
+                ax += c * (F * dx + Fr * dd * d[0]);
+                ay += c * (F * dy + Fr * dd * d[1]);
+                az += c * (F * dz + Fr * dd * d[2]);
+            } else {
+                const T c = Ph.m_g * F * (rhoa + rhob);
+                ax += c * d[0];
+                ay += c * d[1];
+                az += c * d[2];
+            }
+            return;
+        }
         if (MODE <= 1) {
             sum += kernel_w(G, approx_sqrt(r2) * G.inv_h);
             if (MODE == 1) {
@@ -142,6 +185,15 @@ template <class T, int MODE>
 __device__ __forceinline__ void acc_init(PairAcc<T, MODE> &A, const Phys<T> &Ph, const V4<T> &pa,
                                          const V4<T> *__restrict__ vel, const T *__restrict__ rho, uint32_t a)
 {
+    if (MODE == 4) {
+        A.qa = pa.w;
+        A.va = vel[a];  // lambda_A_a
+        return;
+    }
+    if (MODE == 5) {
+        A.rhoa = rho[a];  // lambda_rho_a
+        return;
+    }
     if (MODE >= 2) {
         A.qa = pa.w;
         A.ca = Ph.cs;
@@ -159,6 +211,26 @@ __device__ __forceinline__ void acc_store(const PairAcc<T, MODE> &A, const Phys<
                                           V4<T> *__restrict__ out_acc, int32_t *__restrict__ cnt,
                                           uint64_t *__restrict__ fpr)
 {
+    if (MODE == 4) {
+        // lambda_rho_a = dq/drho lambda_q_a = -cs^2/rho^2 lambda_q_a (isothermal q = cs^2/rho)
+        const T ra = vel == nullptr ? T(1) : out_rho[a];
+        (void)ra;
+        V4<T> o;
+        o.x = A.ax;
+        o.y = A.ay;
+        o.z = A.az;
+        o.w = A.de;  // lambda_q_a, turned into lambda_rho by the caller
+        out_acc[a] = o;
+        return;
+    }
+    if (MODE == 5) {
+        V4<T> o = out_acc[a];
+        o.x += A.ax;
+        o.y += A.ay;
+        o.z += A.az;
+        out_acc[a] = o;
+        return;
+    }
     if (MODE <= 1) {
         const T r = mass * A.sum;
         out_rho[a] = r;
@@ -312,9 +384,9 @@ __device__ __forceinline__ void walk_global(PairAcc<T, MODE> &A, const Geo<T> &G
             const T r2 = pair_r2<T, DIM, true>(G, pa, pb, d);
             V4<T> vb;
             T rhob = T(1);
-            if (MODE == 3 && r2 < G.h2x4) {
-                vb = vel[b];
-                rhob = rho[b];
+            if (r2 < G.h2x4) {
+                if (ModeUses<MODE>::vel) vb = vel[b];
+                if (ModeUses<MODE>::rho) rhob = rho[b];
             }
             A.add(G, Ph, pb, &vb, rhob, MODE == 1 ? id[b] : 0u, r2, d);
         }
@@ -431,8 +503,10 @@ __device__ __forceinline__ void walk_smem_range(PairAcc<T, MODE> &A, const Geo<T
         const V4<T> pb = spos[j];
         T d[3];
         const T r2 = pair_r2<T, DIM, SEAM>(G, pa, pb, d);
-        if (MODE == 3) {
-            if (r2 < G.h2x4) A.add(G, Ph, pb, &svel[j], srho[j], 0u, r2, d);
+        if (ModeUses<MODE>::vel || ModeUses<MODE>::rho) {
+            if (r2 < G.h2x4)
+                A.add(G, Ph, pb, ModeUses<MODE>::vel ? &svel[j] : nullptr, ModeUses<MODE>::rho ? srho[j] : T(1), 0u,
+                      r2, d);
         } else {
             A.add(G, Ph, pb, nullptr, T(1), MODE == 1 ? sid[j] : 0u, r2, d);
         }
@@ -524,8 +598,8 @@ k_pair_tile(Geo<T> G, Phys<T> Ph, TileCfg C, const V4<T> *__restrict__ pos, cons
     int *rowpref = lstart + C.nhalo + 1;               // nrows + 1
     int *rowg = rowpref + C.nrows + 1;                 // nrows
     V4<T> *spos = reinterpret_cast<V4<T> *>(smem + C.offset);
-    V4<T> *svel = spos + C.cap;                        // MODE 3
-    T *srho = reinterpret_cast<T *>(svel + C.cap);     // MODE 3
+    V4<T> *svel = spos + C.cap;                        // modes staging a second V4
+    T *srho = reinterpret_cast<T *>(svel + (ModeUses<MODE>::vel ? C.cap : 0));  // modes staging a scalar
     uint32_t *sid = reinterpret_cast<uint32_t *>(spos + C.cap);  // MODE 1
 
     const int tid = threadIdx.x;
@@ -589,10 +663,8 @@ k_pair_tile(Geo<T> G, Phys<T> Ph, TileCfg C, const V4<T> *__restrict__ pos, cons
             for (int j = j0; j < j1; ++j) {
                 const uint32_t gi = g0 + (uint32_t)(j - j0);
                 spos[j] = pos[gi];
-                if (MODE == 3) {
-                    svel[j] = vel[gi];
-                    srho[j] = rho[gi];
-                }
+                if (ModeUses<MODE>::vel) svel[j] = vel[gi];
+                if (ModeUses<MODE>::rho) srho[j] = rho[gi];
                 if (MODE == 1) sid[j] = id[gi];
             }
         }
@@ -630,8 +702,8 @@ k_pair_tile(Geo<T> G, Phys<T> Ph, TileCfg C, const V4<T> *__restrict__ pos, cons
 // ---------------------------------------------------------------------------
 template <class T, int MODE> constexpr int tile_bytes_per_particle()
 {
-    return MODE == 3 ? (int)(2 * sizeof(V4<T>) + sizeof(T))
-                     : (MODE == 1 ? (int)(sizeof(V4<T>) + 4) : (int)sizeof(V4<T>));
+    return (int)sizeof(V4<T>) + (ModeUses<MODE>::vel ? (int)sizeof(V4<T>) : 0) +
+           (ModeUses<MODE>::rho ? (int)sizeof(T) : 0) + (MODE == 1 ? 4 : 0);
 }
 
 // Tile shape for a phase with `mean` particles per cell. Each CTA thread
@@ -692,7 +764,7 @@ cudaError_t pair_launch(const LaunchCtx &L, const Geo<T> &G, const Phys<T> &Ph, 
                         T *pr_out, V4<T> *out_acc, int32_t *cnt, uint64_t *fpr, double mean)
 {
     constexpr int bpp = tile_bytes_per_particle<T, MODE>();
-    const int budget = MODE == 3 ? 72 * 1024 : 52 * 1024;
+    const int budget = (ModeUses<MODE>::vel || ModeUses<MODE>::rho) ? 72 * 1024 : 52 * 1024;
     TileCfg C{};
     size_t smem = 0;
     if (plan_tiles(G, DIM, mean, bpp, budget, C, smem)) {
@@ -750,7 +822,71 @@ cudaError_t force_t(const LaunchCtx &L, const void *geo, const void *phys, Phase
                                   P.start, nullptr, nullptr, static_cast<V4<T> *>(acc), nullptr, nullptr, mean);
 }
 
+// lambda_A (V4, storage order) -> lambda_x (V4 .xyz) and lambda_q (.w).
+template <class T, int DIM>
+cudaError_t force_adjoint_t(const LaunchCtx &L, const void *geo, const void *phys, PhaseBufs &P, const void *lamA,
+                            void *out)
+{
+    if (P.n == 0) return cudaSuccess;
+    const Geo<T> &G = *static_cast<const Geo<T> *>(geo);
+    const Phys<T> &Ph = *static_cast<const Phys<T> *>(phys);
+    auto *pos = static_cast<const V4<T> *>(P.pos[P.cur]);
+    const double mean = (double)P.n / (double)G.ncells;
+    return pair_launch<T, DIM, 4>(L, G, Ph, (int)P.n, T(0), pos, static_cast<const V4<T> *>(lamA), nullptr,
+                                  P.id[P.cur], P.start, nullptr, nullptr, static_cast<V4<T> *>(out), nullptr, nullptr,
+                                  mean);
+}
+
+// lambda_rho (T, storage order) -> lambda_x (V4 .xyz) accumulated.
+template <class T, int DIM>
+cudaError_t density_adjoint_t(const LaunchCtx &L, const void *geo, const void *phys, PhaseBufs &P,
+                              const void *lamrho, void *inout)
+{
+    if (P.n == 0) return cudaSuccess;
+    const Geo<T> &G = *static_cast<const Geo<T> *>(geo);
+    const Phys<T> &Ph = *static_cast<const Phys<T> *>(phys);
+    auto *pos = static_cast<const V4<T> *>(P.pos[P.cur]);
+    const double mean = (double)P.n / (double)G.ncells;
+    return pair_launch<T, DIM, 5>(L, G, Ph, (int)P.n, T(0), pos, nullptr, static_cast<const T *>(lamrho),
+                                  P.id[P.cur], P.start, nullptr, nullptr, static_cast<V4<T> *>(inout), nullptr,
+                                  nullptr, mean);
+}
+
 }  // namespace
+
+cudaError_t launch_force_adjoint(const LaunchCtx &L, const void *geo, const void *phys, PhaseBufs &G,
+                                 const void *lamA, void *out)
+{
+    if (L.precision == TFSPH_FP64) {
+        switch (L.dim) {
+            case 1: return force_adjoint_t<double, 1>(L, geo, phys, G, lamA, out);
+            case 2: return force_adjoint_t<double, 2>(L, geo, phys, G, lamA, out);
+            default: return force_adjoint_t<double, 3>(L, geo, phys, G, lamA, out);
+        }
+    }
+    switch (L.dim) {
+        case 1: return force_adjoint_t<float, 1>(L, geo, phys, G, lamA, out);
+        case 2: return force_adjoint_t<float, 2>(L, geo, phys, G, lamA, out);
+        default: return force_adjoint_t<float, 3>(L, geo, phys, G, lamA, out);
+    }
+}
+
+cudaError_t launch_density_adjoint(const LaunchCtx &L, const void *geo, const void *phys, PhaseBufs &G,
+                                   const void *lamrho, void *inout)
+{
+    if (L.precision == TFSPH_FP64) {
+        switch (L.dim) {
+            case 1: return density_adjoint_t<double, 1>(L, geo, phys, G, lamrho, inout);
+            case 2: return density_adjoint_t<double, 2>(L, geo, phys, G, lamrho, inout);
+            default: return density_adjoint_t<double, 3>(L, geo, phys, G, lamrho, inout);
+        }
+    }
+    switch (L.dim) {
+        case 1: return density_adjoint_t<float, 1>(L, geo, phys, G, lamrho, inout);
+        case 2: return density_adjoint_t<float, 2>(L, geo, phys, G, lamrho, inout);
+        default: return density_adjoint_t<float, 3>(L, geo, phys, G, lamrho, inout);
+    }
+}
 
 cudaError_t launch_density(const LaunchCtx &L, const void *geo, const void *phys, PhaseBufs &P, void *rho, bool gas,
                            int32_t *cnt, uint64_t *fprint)

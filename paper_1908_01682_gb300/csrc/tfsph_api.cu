@@ -42,6 +42,10 @@ struct tfsph_ctx {
     int *d_flags = nullptr;
     void *staging = nullptr;
     size_t staging_bytes = 0;
+    // adjoint scratch (allocated by the first tfsph_step_adjoint)
+    void *adj_gx4 = nullptr, *adj_gv4 = nullptr, *adj_dx4 = nullptr, *adj_du4 = nullptr;
+    void *adj_lA = nullptr, *adj_out = nullptr, *adj_lrho = nullptr, *adj_lts = nullptr;
+    void *adj_host = nullptr;  // device mirror of host adjoint arrays
     alignas(64) unsigned char geo[sizeof(Geo<double>)];
     alignas(64) unsigned char phys[sizeof(Phys<double>)];
     bool prepared = false;
@@ -591,6 +595,103 @@ int tfsph_profile_read(tfsph_ctx *c, double *ms, int64_t *steps, int64_t *launch
         for (int k = 0; k < TFSPH_PROF_NPHASE; ++k) ms[k] = c->prof_ms[k];
     if (steps) *steps = c->prof_steps;
     if (launches) *launches = c->prof_launches;
+    return TFSPH_OK;
+}
+
+int tfsph_step_adjoint(tfsph_ctx *c, double tau, const double g[3], void *lam_gx, void *lam_gv, void *lam_dx,
+                       void *lam_du, void *lam_ts, int mem_kind)
+{
+    if (!c) return fail(nullptr, TFSPH_E_INVALID_ARG, "ctx is NULL");
+    if (!std::isfinite(tau) || !(tau > 0)) return fail(c, TFSPH_E_INVALID_ARG, "tau must be finite and > 0");
+    if (c->p.eos != TFSPH_EOS_ISOTHERMAL || c->p.av_alpha > 0 || c->p.av_beta > 0)
+        return fail(c, TFSPH_E_INVALID_ARG, "the adjoint covers the isothermal gas without artificial viscosity");
+    if (mem_kind != TFSPH_MEM_HOST && mem_kind != TFSPH_MEM_DEVICE) return fail(c, TFSPH_E_INVALID_ARG, "bad mem_kind");
+    const int64_t ng = c->G.n, nd = c->D.n;
+    if ((ng > 0 && (!lam_gx || !lam_gv)) || (nd > 0 && (!lam_dx || !lam_du || !lam_ts)))
+        return fail(c, TFSPH_E_INVALID_ARG, "NULL adjoint array");
+    double gg[3] = {0, 0, 0};
+    if (g)
+        for (int k = 0; k < 3; ++k) {
+            if (!std::isfinite(g[k])) return fail(c, TFSPH_E_NONFINITE, "non-finite gravity");
+            gg[k] = k < c->dim ? g[k] : 0.0;
+        }
+    int rc;
+    const size_t v4 = 4 * c->tsize, d = (size_t)c->dim;
+    if (!c->adj_gx4) {
+        if ((rc = dalloc(c, &c->adj_gx4, (size_t)ng * v4))) return rc;
+        if ((rc = dalloc(c, &c->adj_gv4, (size_t)ng * v4))) return rc;
+        if ((rc = dalloc(c, &c->adj_dx4, (size_t)nd * v4))) return rc;
+        if ((rc = dalloc(c, &c->adj_du4, (size_t)nd * v4))) return rc;
+        if ((rc = dalloc(c, &c->adj_lA, (size_t)ng * v4))) return rc;
+        if ((rc = dalloc(c, &c->adj_out, (size_t)ng * v4))) return rc;
+        if ((rc = dalloc(c, &c->adj_lrho, (size_t)ng * c->tsize))) return rc;
+        if ((rc = dalloc(c, &c->adj_lts, (size_t)nd * c->tsize))) return rc;
+    }
+    // device views of the caller's arrays (component-major, id order)
+    void *dgx = lam_gx, *dgv = lam_gv, *ddx = lam_dx, *ddu = lam_du, *dts = lam_ts;
+    const size_t bg = d * (size_t)ng * c->tsize, bd = d * (size_t)nd * c->tsize, bt = (size_t)nd * c->tsize;
+    if (mem_kind == TFSPH_MEM_HOST) {
+        if (!c->adj_host && (rc = dalloc(c, &c->adj_host, 2 * bg + 2 * bd + bt))) return rc;
+        char *base = static_cast<char *>(c->adj_host);
+        dgx = base;
+        dgv = base + bg;
+        ddx = base + 2 * bg;
+        ddu = base + 2 * bg + bd;
+        dts = base + 2 * bg + 2 * bd;
+        if (ng > 0) {
+            TF_CUDA(c, cudaMemcpyAsync(dgx, lam_gx, bg, cudaMemcpyHostToDevice, c->stream));
+            TF_CUDA(c, cudaMemcpyAsync(dgv, lam_gv, bg, cudaMemcpyHostToDevice, c->stream));
+        }
+        if (nd > 0) {
+            TF_CUDA(c, cudaMemcpyAsync(ddx, lam_dx, bd, cudaMemcpyHostToDevice, c->stream));
+            TF_CUDA(c, cudaMemcpyAsync(ddu, lam_du, bd, cudaMemcpyHostToDevice, c->stream));
+            TF_CUDA(c, cudaMemcpyAsync(dts, lam_ts, bt, cudaMemcpyHostToDevice, c->stream));
+        }
+    }
+    LaunchCtx L = lctx(c);
+    // forward quantities of the step: binning, density, pressure acceleration
+    if ((rc = prepare(c))) return rc;
+    if (ng > 0) TF_CUDA(c, launch_force(L, c->geo, c->phys, c->G, c->rho_g, c->acc));
+    // adjoint vectors into storage order
+    TF_CUDA(c, launch_lam_gather(L, c->G, dgx, c->adj_gx4));
+    TF_CUDA(c, launch_lam_gather(L, c->G, dgv, c->adj_gv4));
+    TF_CUDA(c, launch_lam_gather(L, c->D, ddx, c->adj_dx4));
+    TF_CUDA(c, launch_lam_gather(L, c->D, ddu, c->adj_du4));
+    if (nd > 0) TF_CUDA(c, cudaMemsetAsync(c->adj_lts, 0, bt, c->stream));
+    StepArgs S;
+    S.tau = tau;
+    S.g[0] = gg[0];
+    S.g[1] = gg[1];
+    S.g[2] = gg[2];
+    S.tstar_mode = c->p.tstar_mode;
+    S.cell_acc = c->cell_acc;
+    S.has_frozen = c->has_frozen ? 1 : 0;
+    // update and cell drag -> lambda_A, lambda_v, lambda_u, lambda_t_stop
+    TF_CUDA(c, launch_cell_adjoint(L, c->geo, c->phys, c->G, c->D, c->acc, S, c->adj_gx4, c->adj_gv4, c->adj_dx4,
+                                   c->adj_du4, c->adj_lA, c->adj_lts));
+    if (ng > 0) {
+        // pressure force -> lambda_x (through d_ab) and lambda_q; q = cs^2/rho -> lambda_rho; density -> lambda_x
+        TF_CUDA(c, launch_force_adjoint(L, c->geo, c->phys, c->G, c->adj_lA, c->adj_out));
+        TF_CUDA(c, launch_lamq_to_lamrho(L, c->G, c->adj_out, c->rho_g, c->p.cs * c->p.cs, c->adj_lrho));
+        TF_CUDA(c, launch_density_adjoint(L, c->geo, c->phys, c->G, c->adj_lrho, c->adj_out));
+        TF_CUDA(c, launch_lam_scatter(L, c->G, c->adj_gx4, c->adj_out, dgx));
+        TF_CUDA(c, launch_lam_scatter(L, c->G, c->adj_gv4, nullptr, dgv));
+    }
+    if (nd > 0) {
+        TF_CUDA(c, launch_lam_scatter(L, c->D, c->adj_du4, nullptr, ddu));
+        TF_CUDA(c, launch_lam_add_scalar(L, c->D, c->adj_lts, dts));
+    }
+    if (mem_kind == TFSPH_MEM_HOST) {
+        if (ng > 0) {
+            TF_CUDA(c, cudaMemcpyAsync(lam_gx, dgx, bg, cudaMemcpyDeviceToHost, c->stream));
+            TF_CUDA(c, cudaMemcpyAsync(lam_gv, dgv, bg, cudaMemcpyDeviceToHost, c->stream));
+        }
+        if (nd > 0) {
+            TF_CUDA(c, cudaMemcpyAsync(lam_du, ddu, bd, cudaMemcpyDeviceToHost, c->stream));
+            TF_CUDA(c, cudaMemcpyAsync(lam_ts, dts, bt, cudaMemcpyDeviceToHost, c->stream));
+        }
+        TF_CUDA(c, cudaStreamSynchronize(c->stream));
+    }
     return TFSPH_OK;
 }
 

@@ -127,12 +127,21 @@ cudaError_t launch_check(const LaunchCtx &L, const void *geo, const PhaseBufs &P
 cudaError_t launch_max_speed(const LaunchCtx &L, const void *phys, const PhaseBufs &G,
                              void *partials, int nblk, void *result);
 cudaError_t launch_debug_keys(const LaunchCtx &L, const void *geo, const PhaseBufs &P, uint32_t *out);
+cudaError_t launch_lam_gather(const LaunchCtx &L, const PhaseBufs &P, const void *lam, void *out);
+cudaError_t launch_lam_scatter(const LaunchCtx &L, const PhaseBufs &P, const void *a, const void *b, void *lam);
+cudaError_t launch_lam_add_scalar(const LaunchCtx &L, const PhaseBufs &P, const void *src, void *dst);
+cudaError_t launch_lamq_to_lamrho(const LaunchCtx &L, const PhaseBufs &P, const void *lq, const void *rho, double cs2,
+                                  void *lrho);
 
 // sph.cu
 cudaError_t launch_density(const LaunchCtx &L, const void *geo, const void *phys, PhaseBufs &P,
                            void *rho, bool gas, int32_t *cnt, uint64_t *fprint);
 cudaError_t launch_force(const LaunchCtx &L, const void *geo, const void *phys, PhaseBufs &G,
                          const void *rho, void *acc);
+cudaError_t launch_force_adjoint(const LaunchCtx &L, const void *geo, const void *phys, PhaseBufs &G,
+                                 const void *lamA, void *out);
+cudaError_t launch_density_adjoint(const LaunchCtx &L, const void *geo, const void *phys, PhaseBufs &G,
+                                   const void *lamrho, void *inout);
 
 // tfsph_api.cu: message for tfsph_last_error(NULL) from calls without a context
 void set_unbound_error(const char *msg);
@@ -147,6 +156,9 @@ struct StepArgs {
 };
 cudaError_t launch_cell_update(const LaunchCtx &L, const void *geo, const void *phys,
                                PhaseBufs &G, PhaseBufs &D, const void *acc, const StepArgs &S);
+cudaError_t launch_cell_adjoint(const LaunchCtx &L, const void *geo, const void *phys, PhaseBufs &G, PhaseBufs &D,
+                                const void *acc, const StepArgs &S, const void *lgx, void *lgv, const void *ldx,
+                                void *ldu, void *lA, void *lts);
 
 // ---------------------------------------------------------------------------
 // Device helpers shared by the kernels.
@@ -232,6 +244,14 @@ template <class T> __device__ __forceinline__ T kernel_f(const Geo<T> &G, T q, T
 {
     const T a = fmax(T(2) - q, T(0));
     return G.fnorm * (q < T(1) ? T(-3) + T(2.25) * q : T(-0.75) * a * a * inv_q);
+}
+
+// d/dr of (1/r) dW/dr:
+//   fnorm / h * (q < 1 ? 9/4 : 3/4 (2 - q)(2 + q) / q^2)
+template <class T> __device__ __forceinline__ T kernel_fprime(const Geo<T> &G, T q, T inv_q)
+{
+    const T a = fmax(T(2) - q, T(0));
+    return G.fnorm * G.inv_h * (q < T(1) ? T(2.25) : T(0.75) * a * (q + T(2)) * inv_q * inv_q);
 }
 
 }  // namespace tfsph
