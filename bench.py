@@ -47,6 +47,7 @@ def parse_args(argv=None):
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-clocks", action="store_true")
+    ap.add_argument("--no-adjoint", action="store_true")
     return ap.parse_args(argv)
 
 
@@ -391,6 +392,10 @@ def run_ours(args, dist: Dist):
     if not args.no_e2e:
         e2e = run_e2e(b, ctx, w, args, dist)
 
+    adj = None
+    if not args.no_adjoint:
+        adj = run_adjoint(b, args)
+
     cpu = None
     if dist.rank == 0 and dist.world == 1 and not args.no_cpu_baseline:
         cpu = cpu_baseline(args.workload, 0)
@@ -406,10 +411,52 @@ def run_ours(args, dist: Dist):
         "clocks": clk, "e2e": e2e, "gpu_launches": int(launches),
         "roofline": roof,
         "kernel_ms": {k: round(v, 5) for k, v in phase_avg.items()},
+        "adjoint": adj,
         "cpu_baseline": cpu,
     }
     if dist.rank == 0:
         print(json.dumps(line), flush=True)
+
+
+def run_adjoint(b, args):
+    """Adjoint cost: a checkpointed rollout on the 2D settling column (512^2 +
+    512^2, FP32) - forward of K steps vs the backward (segment recompute +
+    step adjoints), both through the library, wall time with synchronisation."""
+    import numpy as np
+    import torch
+
+    from paper_1908_01682_gb300 import adjoint
+
+    w, desc = make_workload("column2d")
+    p = b.params_from_dict(w.params)
+    f32 = lambda a: np.ascontiguousarray(a, dtype=np.float32)
+    nsteps, every = 20, 10
+    with b.Context(p, f32(w.gx), f32(w.gv), f32(w.dx), f32(w.du), f32(w.tstop), frozen=w.frozen) as c:
+        c.set_stream(torch.cuda.current_stream())
+        dev = lambda a: torch.tensor(f32(a), device="cuda")
+        st0 = (dev(w.gx), dev(w.gv), dev(w.dx), dev(w.du), dev(w.tstop))
+        roll = adjoint.Rollout(c, w.tau, w.g, nsteps, checkpoint_every=every, frozen=w.frozen)
+        # warm-up of both directions
+        roll.forward(st0)
+        lam = [torch.ones_like(t) for t in st0[:4]]
+        roll.backward(*lam)
+        torch.cuda.synchronize()
+        roll.restore(st0)
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        for _ in range(nsteps):
+            c.step(w.tau, w.g)
+        torch.cuda.synchronize()
+        fwd = time.perf_counter() - t0
+        roll.forward(st0)
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        roll.backward(*lam)
+        torch.cuda.synchronize()
+        bwd = time.perf_counter() - t0
+    return {"workload": desc, "steps": nsteps, "checkpoint_every": every, "forward_ms": fwd * 1e3,
+            "backward_ms": bwd * 1e3, "ratio": bwd / fwd,
+            "note": "backward = per-segment recompute + state restores + step adjoints"}
 
 
 def run_e2e(b, ctx, w, args, dist):

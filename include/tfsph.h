@@ -186,6 +186,26 @@ int tfsph_step(tfsph_ctx *c, double tau, const void *t_stop, int mem_kind, const
 int tfsph_step_adjoint(tfsph_ctx *c, double tau, const double g[3], void *lam_gx, void *lam_gv,
                        void *lam_dx, void *lam_du, void *lam_ts, int mem_kind);
 
+/* Checkpoint / resume: a raw snapshot of the context's particle state
+ * (positions, velocities, energies, stopping times, ids, in the library's
+ * storage order), its step count, and the state's forward quantities (cell
+ * ranges, gas densities and pressure accelerations, Eqs. 17-19), which
+ * tfsph_save_state computes first if the context does not hold them yet.
+ * Loading a snapshot leaves the context as a step finds it after binning,
+ * density and force, so the next tfsph_step or tfsph_step_adjoint starts
+ * from the update (this is what makes a checkpointed reverse pass cost one
+ * force evaluation per step). tfsph_state_bytes gives the size; save and
+ * load copy to/from a caller-owned buffer of mem_kind (device copies are
+ * asynchronous on the context's stream; host copies synchronise). A snapshot
+ * loads only into a context of the same counts, dimension, precision and
+ * cell grid: INVALID_ARG from a host buffer; for a device buffer the header
+ * is checked on the device and a mismatch is reported by the next
+ * tfsph_sync (INTERNAL). Loading a device snapshot keeps the context's step
+ * count. */
+int tfsph_state_bytes(const tfsph_ctx *c, int64_t *bytes);
+int tfsph_save_state(tfsph_ctx *c, void *buf, int mem_kind);
+int tfsph_load_state(tfsph_ctx *c, const void *buf, int mem_kind);
+
 /* Courant step (Eq. 4): *tau_out = cfl * h / max over moving gas of
  * max(|v_a|, c_a). Synchronises the stream. */
 int tfsph_max_dt(tfsph_ctx *c, double cfl, double *tau_out);

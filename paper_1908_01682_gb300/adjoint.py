@@ -5,6 +5,9 @@
 from its checkpoint (keeping the segment's per-step states) and applies the
 library's hand-written step adjoint (``tfsph_step_adjoint``) in reverse,
 so memory grows with the checkpoint interval, not with the rollout length.
+A snapshot carries its state's binning, density and pressure acceleration,
+so each step's force is evaluated once in the recompute and reused by the
+adjoint after the snapshot is loaded.
 
 ``TFSPHRollout`` wraps it in a ``torch.autograd.Function``: gradients of any
 loss on the final state with respect to the per-particle stopping times and
@@ -29,7 +32,9 @@ class Rollout:
         self.dim = ctx.dim
         self.dtype = torch.float64 if ctx.params.precision == b.TFSPH_FP64 else torch.float32
         self.frozen = None if frozen is None else torch.as_tensor(frozen, dtype=torch.uint8, device="cuda")
-        self.checkpoints = []
+        self.checkpoints = []   # device snapshots (tfsph_save_state) every `every` steps
+        self.inputs = None      # the initial state as given
+        self._segment = []      # snapshot buffers reused by the backward's recompute
 
     # state = (gx, gv, dx, du, tstop), device tensors in id order
     def export(self):
@@ -49,29 +54,34 @@ class Rollout:
         self.ctx.set_state(gx, gv, dx, du, ts, frozen=self.frozen)
 
     def forward(self, state0):
-        self.checkpoints = [tuple(t.detach().clone() for t in state0)]
-        self.restore(self.checkpoints[0])
+        self.inputs = tuple(t.detach().clone() for t in state0)
+        self.restore(self.inputs)
+        self.checkpoints = [self.ctx.save_state()]
         for i in range(self.nsteps):
             self.ctx.step(self.tau, self.g)
             if (i + 1) % self.every == 0 and i + 1 < self.nsteps:
-                self.checkpoints.append(self.export())
+                self.checkpoints.append(self.ctx.save_state())
         return self.export()
 
     def backward(self, lam_gx, lam_gv, lam_dx, lam_du):
         """Adjoints of the final state -> adjoints of the initial state and of t_stop."""
         lam = [t.detach().clone().contiguous() for t in (lam_gx, lam_gv, lam_dx, lam_du)]
         lam_ts = torch.zeros(self.ctx.n_dust, dtype=self.dtype, device="cuda")
+        while len(self._segment) < self.every:
+            self._segment.append(self.ctx.save_state())
         nseg = (self.nsteps + self.every - 1) // self.every
         for seg in reversed(range(nseg)):
             start = seg * self.every
             end = min(self.nsteps, start + self.every)
-            self.restore(self.checkpoints[seg])
-            states = []
-            for _ in range(start, end):
-                states.append(self.export())
+            self.ctx.load_state(self.checkpoints[seg])
+            # recompute the segment's step-start states; the last step's
+            # output is not needed, so the context ends at the last start state
+            for i in range(end - start - 1):
+                self.ctx.save_state(self._segment[i])
                 self.ctx.step(self.tau, self.g)
             for i in reversed(range(end - start)):
-                self.restore(states[i])
+                if i < end - start - 1:
+                    self.ctx.load_state(self._segment[i])
                 self.ctx.step_adjoint(self.tau, self.g, lam[0], lam[1], lam[2], lam[3], lam_ts)
         return lam[0], lam[1], lam[2], lam[3], lam_ts
 
@@ -90,7 +100,7 @@ class TFSPHRollout(torch.autograd.Function):
     def backward(fctx, lgx, lgv, ldx, ldu):
         r = fctx.rollout
         z = lambda like, t: torch.zeros_like(like) if t is None else t
-        ref = r.checkpoints[0]
+        ref = r.inputs
         lgx, lgv, ldx, ldu = z(ref[0], lgx), z(ref[1], lgv), z(ref[2], ldx), z(ref[3], ldu)
         l0 = r.backward(lgx, lgv, ldx, ldu)
         return l0[4], l0[1], l0[3], None, None, None

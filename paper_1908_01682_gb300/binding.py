@@ -88,6 +88,9 @@ def load() -> C.CDLL:
     lib.tfsph_step.argtypes = [ctxp, d, vp, i32, C.POINTER(d)]
     lib.tfsph_max_dt.argtypes = [ctxp, d, C.POINTER(d)]
     lib.tfsph_step_adjoint.argtypes = [ctxp, d, C.POINTER(d), vp, vp, vp, vp, vp, i32]
+    lib.tfsph_state_bytes.argtypes = [ctxp, C.POINTER(i64)]
+    lib.tfsph_save_state.argtypes = [ctxp, vp, i32]
+    lib.tfsph_load_state.argtypes = [ctxp, vp, i32]
     lib.tfsph_fields.argtypes = [ctxp, i32, vp, i32, i32]
     lib.tfsph_debug.argtypes = [ctxp, i32, vp, i32]
     lib.tfsph_info.argtypes = [ctxp, C.POINTER(tfsph_info_t)]
@@ -104,7 +107,8 @@ def load() -> C.CDLL:
     lib.tfsph_version.argtypes = []
     for name in ("tfsph_init", "tfsph_set_state", "tfsph_set_stream", "tfsph_step", "tfsph_step_adjoint", "tfsph_max_dt",
                  "tfsph_fields", "tfsph_debug", "tfsph_info", "tfsph_sync", "tfsph_version",
-                 "tfsph_profile", "tfsph_profile_read", "tfsph_cell_ranges_noalloc"):
+                 "tfsph_profile", "tfsph_profile_read", "tfsph_cell_ranges_noalloc", "tfsph_state_bytes",
+                 "tfsph_save_state", "tfsph_load_state"):
         getattr(lib, name).restype = C.c_int
     _lib = lib
     return lib
@@ -142,6 +146,20 @@ def tfsph_step(ctx, tau: float, tstop_ptr, mem_kind: int, g) -> int:
 def tfsph_step_adjoint(ctx, tau: float, g, lam_gx, lam_gv, lam_dx, lam_du, lam_ts, mem_kind: int) -> int:
     g3 = (C.c_double * 3)(*[float(g[k]) if k < len(g) else 0.0 for k in range(3)])
     return load().tfsph_step_adjoint(ctx, float(tau), g3, lam_gx, lam_gv, lam_dx, lam_du, lam_ts, int(mem_kind))
+
+
+def tfsph_state_bytes(ctx):
+    n = C.c_int64(0)
+    rc = load().tfsph_state_bytes(ctx, C.byref(n))
+    return rc, n.value
+
+
+def tfsph_save_state(ctx, buf_ptr, mem_kind: int) -> int:
+    return load().tfsph_save_state(ctx, buf_ptr, int(mem_kind))
+
+
+def tfsph_load_state(ctx, buf_ptr, mem_kind: int) -> int:
+    return load().tfsph_load_state(ctx, buf_ptr, int(mem_kind))
 
 
 def tfsph_max_dt(ctx, cfl: float):
@@ -312,6 +330,29 @@ class Context:
             ptrs = [a.ctypes.data for a in arrs]
             mem = TFSPH_MEM_HOST
         _check(tfsph_step_adjoint(self.ctx, tau, g, *ptrs, mem), self.ctx)
+
+    def state_bytes(self) -> int:
+        rc, n = tfsph_state_bytes(self.ctx)
+        _check(rc, self.ctx)
+        return n
+
+    def save_state(self, buf=None):
+        """Snapshot into ``buf`` (torch CUDA uint8 tensor or numpy uint8 array;
+        a new device tensor when None)."""
+        if buf is None:
+            import torch
+            buf = torch.empty(self.state_bytes(), dtype=torch.uint8, device="cuda")
+        if _is_torch(buf):
+            _check(tfsph_save_state(self.ctx, buf.data_ptr(), TFSPH_MEM_DEVICE), self.ctx)
+        else:
+            _check(tfsph_save_state(self.ctx, buf.ctypes.data, TFSPH_MEM_HOST), self.ctx)
+        return buf
+
+    def load_state(self, buf):
+        if _is_torch(buf):
+            _check(tfsph_load_state(self.ctx, buf.data_ptr(), TFSPH_MEM_DEVICE), self.ctx)
+        else:
+            _check(tfsph_load_state(self.ctx, np.ascontiguousarray(buf).ctypes.data, TFSPH_MEM_HOST), self.ctx)
 
     def max_dt(self, cfl: float) -> float:
         rc, tau = tfsph_max_dt(self.ctx, cfl)

@@ -48,7 +48,8 @@ struct tfsph_ctx {
     void *adj_host = nullptr;  // device mirror of host adjoint arrays
     alignas(64) unsigned char geo[sizeof(Geo<double>)];
     alignas(64) unsigned char phys[sizeof(Phys<double>)];
-    bool prepared = false;
+    bool prepared = false;      // binning and density of the current state are done
+    bool forced = false;        // ... and acc holds its pressure acceleration
     bool counts_dirty = false;  // a binning did not finish: zero the cell counts first
     bool has_frozen = false;
     int64_t steps = 0;
@@ -285,6 +286,7 @@ int load_state(tfsph_ctx *c, const void *const *gas, const void *const *dust, co
     }
     c->has_frozen = any_frozen;
     c->prepared = false;
+    c->forced = false;
     c->steps = 0;
     return TFSPH_OK;
 }
@@ -344,6 +346,22 @@ int prepare(tfsph_ctx *c, cudaEvent_t *ev = nullptr)
     if (c->G.n > 0) c->launches += 1;
     if (ev) TF_CUDA(c, cudaEventRecord(ev[TFSPH_PROF_DENSITY + 1], c->stream));
     c->prepared = true;
+    return TFSPH_OK;
+}
+
+// Binning, density and pressure acceleration of the current state (what the
+// step and its adjoint both start from); done once per state.
+int forward_quantities(tfsph_ctx *c, cudaEvent_t *ev = nullptr)
+{
+    int rc = prepare(c, ev);
+    if (rc) return rc;
+    if (c->G.n > 0 && !c->forced) {
+        LaunchCtx L = lctx(c);
+        TF_CUDA(c, launch_force(L, c->geo, c->phys, c->G, c->rho_g, c->acc));
+        c->launches += 1;
+    }
+    c->forced = true;
+    if (ev) TF_CUDA(c, cudaEventRecord(ev[TFSPH_PROF_FORCE + 1], c->stream));
     return TFSPH_OK;
 }
 
@@ -545,13 +563,8 @@ int tfsph_step(tfsph_ctx *c, double tau, const void *t_stop, int mem_kind, const
     int rc = next_events(c, &ev);
     if (rc) return rc;
     if (ev) TF_CUDA(c, cudaEventRecord(ev[0], c->stream));
-    rc = prepare(c, ev);
+    rc = forward_quantities(c, ev);
     if (rc) return rc;
-    if (c->G.n > 0) {
-        TF_CUDA(c, launch_force(L, c->geo, c->phys, c->G, c->rho_g, c->acc));
-        c->launches += 1;
-    }
-    if (ev) TF_CUDA(c, cudaEventRecord(ev[TFSPH_PROF_FORCE + 1], c->stream));
     StepArgs S;
     S.tau = tau;
     S.g[0] = gg[0];
@@ -568,6 +581,7 @@ int tfsph_step(tfsph_ctx *c, double tau, const void *t_stop, int mem_kind, const
         c->prof_launches += c->launches - launches0;
     }
     c->prepared = false;
+    c->forced = false;
     c->steps += 1;
     return TFSPH_OK;
 }
@@ -650,8 +664,7 @@ int tfsph_step_adjoint(tfsph_ctx *c, double tau, const double g[3], void *lam_gx
     }
     LaunchCtx L = lctx(c);
     // forward quantities of the step: binning, density, pressure acceleration
-    if ((rc = prepare(c))) return rc;
-    if (ng > 0) TF_CUDA(c, launch_force(L, c->geo, c->phys, c->G, c->rho_g, c->acc));
+    if ((rc = forward_quantities(c))) return rc;
     // adjoint vectors into storage order
     TF_CUDA(c, launch_lam_gather(L, c->G, dgx, c->adj_gx4));
     TF_CUDA(c, launch_lam_gather(L, c->G, dgv, c->adj_gv4));
@@ -692,6 +705,128 @@ int tfsph_step_adjoint(tfsph_ctx *c, double tau, const double g[3], void *lam_gx
         }
         TF_CUDA(c, cudaStreamSynchronize(c->stream));
     }
+    return TFSPH_OK;
+}
+
+// Snapshot blob: the header; for gas and dust in storage order (the order of
+// the binning below) pos, vel (V4) and id; then the state's forward
+// quantities: the cell starts of gas and dust (ncells + 1 each), the gas
+// densities and the gas pressure accelerations (V4). Loading one leaves the
+// context as a step would find it after its binning, density and force.
+namespace {
+struct SnapHeader {
+    uint64_t magic;  // "TFSPHST2"
+    int64_t n_gas, n_dust, steps;
+    int32_t dim, precision;
+    uint32_t ncells, reserved0;
+    uint64_t reserved[3];
+};
+constexpr uint64_t kSnapMagic = 0x3254535048504654ull;
+
+__global__ void k_check_snapshot(const SnapHeader *h, int64_t ng, int64_t nd, int dim, int precision,
+                                 uint32_t ncells, int *err)
+{
+    if (h->magic != kSnapMagic || h->n_gas != ng || h->n_dust != nd || h->dim != dim || h->precision != precision ||
+        h->ncells != ncells)
+        atomicOr(err, kErrInternal);
+}
+
+// One region of the blob: a device array of the context and its size.
+struct SnapPart {
+    void *ptr;
+    size_t bytes;
+};
+
+std::vector<SnapPart> snap_parts(tfsph_ctx *c)
+{
+    const size_t v4 = 4 * c->tsize, nc = (size_t)c->ncells + 1;
+    std::vector<SnapPart> parts;
+    for (PhaseBufs *P : {&c->G, &c->D}) {
+        const size_t n = (size_t)P->n;
+        parts.push_back({P->pos[P->cur], n * v4});
+        parts.push_back({P->vel[P->cur], n * v4});
+        parts.push_back({P->id[P->cur], n * 4});
+    }
+    parts.push_back({c->G.start, nc * 4});
+    parts.push_back({c->D.start, nc * 4});
+    parts.push_back({c->rho_g, (size_t)c->G.n * c->tsize});
+    parts.push_back({c->acc, (size_t)c->G.n * v4});
+    return parts;
+}
+}  // namespace
+
+int tfsph_state_bytes(const tfsph_ctx *c, int64_t *bytes)
+{
+    if (!c || !bytes) return TFSPH_E_INVALID_ARG;
+    size_t total = sizeof(SnapHeader);
+    for (const SnapPart &q : snap_parts(const_cast<tfsph_ctx *>(c))) total += q.bytes;
+    *bytes = (int64_t)total;
+    return TFSPH_OK;
+}
+
+int tfsph_save_state(tfsph_ctx *c, void *buf, int mem_kind)
+{
+    if (!c) return fail(nullptr, TFSPH_E_INVALID_ARG, "ctx is NULL");
+    if (!buf) return fail(c, TFSPH_E_INVALID_ARG, "buf is NULL");
+    if (mem_kind != TFSPH_MEM_HOST && mem_kind != TFSPH_MEM_DEVICE) return fail(c, TFSPH_E_INVALID_ARG, "bad mem_kind");
+    int rc = forward_quantities(c);
+    if (rc) return rc;
+    SnapHeader h{};
+    h.magic = kSnapMagic;
+    h.n_gas = c->G.n;
+    h.n_dust = c->D.n;
+    h.steps = c->steps;
+    h.dim = c->dim;
+    h.precision = c->precision;
+    h.ncells = c->ncells;
+    const cudaMemcpyKind k = mem_kind == TFSPH_MEM_DEVICE ? cudaMemcpyDeviceToDevice : cudaMemcpyDeviceToHost;
+    char *dst = static_cast<char *>(buf);
+    if (mem_kind == TFSPH_MEM_DEVICE) TF_CUDA(c, cudaMemcpyAsync(dst, &h, sizeof h, cudaMemcpyHostToDevice, c->stream));
+    else memcpy(dst, &h, sizeof h);
+    dst += sizeof h;
+    for (const SnapPart &q : snap_parts(c)) {
+        if (q.bytes) TF_CUDA(c, cudaMemcpyAsync(dst, q.ptr, q.bytes, k, c->stream));
+        dst += q.bytes;
+    }
+    if (mem_kind == TFSPH_MEM_HOST) TF_CUDA(c, cudaStreamSynchronize(c->stream));  // complete on return
+    return TFSPH_OK;
+}
+
+int tfsph_load_state(tfsph_ctx *c, const void *buf, int mem_kind)
+{
+    if (!c) return fail(nullptr, TFSPH_E_INVALID_ARG, "ctx is NULL");
+    if (!buf) return fail(c, TFSPH_E_INVALID_ARG, "buf is NULL");
+    if (mem_kind != TFSPH_MEM_HOST && mem_kind != TFSPH_MEM_DEVICE) return fail(c, TFSPH_E_INVALID_ARG, "bad mem_kind");
+    SnapHeader h{};
+    const char *src = static_cast<const char *>(buf);
+    if (mem_kind == TFSPH_MEM_DEVICE) {
+        // checked on the device, without a host round trip; a mismatch is
+        // reported by the next tfsph_sync (the copies below use this
+        // context's sizes, so they stay in bounds either way)
+        k_check_snapshot<<<1, 1, 0, c->stream>>>(reinterpret_cast<const SnapHeader *>(src), c->G.n, c->D.n, c->dim,
+                                                 c->precision, c->ncells, c->d_err);
+        TF_CUDA(c, cudaGetLastError());
+        c->launches += 1;
+        h.steps = -1;
+    } else {
+        memcpy(&h, src, sizeof h);
+        if (h.magic != kSnapMagic || h.n_gas != c->G.n || h.n_dust != c->D.n || h.dim != c->dim ||
+            h.precision != c->precision || h.ncells != c->ncells)
+            return fail(c, TFSPH_E_INVALID_ARG, "snapshot does not belong to a context of this shape");
+    }
+    const cudaMemcpyKind k = mem_kind == TFSPH_MEM_DEVICE ? cudaMemcpyDeviceToDevice : cudaMemcpyHostToDevice;
+    src += sizeof h;
+    for (const SnapPart &q : snap_parts(c)) {
+        if (q.bytes) TF_CUDA(c, cudaMemcpyAsync(q.ptr, src, q.bytes, k, c->stream));
+        src += q.bytes;
+    }
+    if (mem_kind == TFSPH_MEM_HOST) TF_CUDA(c, cudaStreamSynchronize(c->stream));
+    // the cell keys are rewritten by the step's update before the next binning;
+    // the per-cell counters are cleared by that binning
+    c->prepared = true;
+    c->forced = true;
+    c->counts_dirty = true;
+    if (h.steps >= 0) c->steps = h.steps;
     return TFSPH_OK;
 }
 

@@ -327,3 +327,69 @@ def test_dustyshock_full_size_one_step(orc):
 
 def test_column2d_full_size_one_step(orc):
     _compare(orc, workloads.column2d(nside=512, precision=0))
+
+
+def test_save_and_load_state_resume_bit_for_bit(orc):
+    """A snapshot taken mid-run and loaded back resumes the run exactly."""
+    torch = pytest.importorskip("torch")
+    b = gpu_lib()
+    w = workloads.column2d(nside=24, precision=0)
+    with gpu_context(w) as c:
+        for _ in range(3):
+            c.step(w.tau, w.g)
+        snap = c.save_state()
+        host = c.save_state(np.zeros(c.state_bytes(), np.uint8))
+        for _ in range(4):
+            c.step(w.tau, w.g)
+        ref = c.field(b.TFSPH_FIELD_VEL_D)
+        c.load_state(snap)
+        assert c.info().steps == 7          # a device load keeps the step count
+        for _ in range(4):
+            c.step(w.tau, w.g)
+        again = c.field(b.TFSPH_FIELD_VEL_D)
+        c.load_state(host)
+        assert c.info().steps == 3          # a host load restores it
+        for _ in range(4):
+            c.step(w.tau, w.g)
+        again_host = c.field(b.TFSPH_FIELD_VEL_D)
+    assert np.array_equal(ref, again) and np.array_equal(ref, again_host)
+    # a snapshot of another shape is refused (host: at once; device: at the next sync)
+    w2 = workloads.column2d(nside=16, precision=0)
+    with gpu_context(w2) as c2:
+        with pytest.raises(b.TfsphError):
+            c2.load_state(host)
+        c2.sync()
+        c2.load_state(snap[: c2.state_bytes()])
+        with pytest.raises(b.TfsphError):
+            c2.sync()
+
+
+def test_step_adjoint_after_load_reuses_forward_quantities(orc):
+    """The adjoint of a step started from a loaded snapshot (which carries the
+    state's binning, density and pressure acceleration) equals the adjoint
+    computed from the plain state, bit for bit."""
+    torch = pytest.importorskip("torch")
+    b = gpu_lib()
+    w = workloads.column2d(nside=24, precision=0)
+    with gpu_context(w) as c:
+        for _ in range(2):
+            c.step(w.tau, w.g)
+        snap = c.save_state()
+        gen = torch.Generator(device="cpu").manual_seed(5)
+        lam0 = [torch.randn(c.dim, c.n_gas, generator=gen), torch.randn(c.dim, c.n_gas, generator=gen),
+                torch.randn(c.dim, c.n_dust, generator=gen), torch.randn(c.dim, c.n_dust, generator=gen)]
+        outs = []
+        for use_snapshot in (False, True):
+            if use_snapshot:
+                c.load_state(snap)
+            else:
+                # the same state without its forward quantities
+                st = (c.field(b.TFSPH_FIELD_POS_G), c.field(b.TFSPH_FIELD_VEL_G), c.field(b.TFSPH_FIELD_POS_D),
+                      c.field(b.TFSPH_FIELD_VEL_D), c.field(b.TFSPH_FIELD_TSTOP_D))
+                c.set_state(*st, frozen=w.frozen)
+            lam = [t.clone().cuda() for t in lam0]
+            lts = torch.zeros(c.n_dust, dtype=torch.float32, device="cuda")
+            c.step_adjoint(w.tau, w.g, lam[0], lam[1], lam[2], lam[3], lts)
+            outs.append([t.cpu().numpy() for t in lam + [lts]])
+    for a, r in zip(outs[1], outs[0]):
+        assert np.array_equal(a, r)
