@@ -50,6 +50,7 @@ extern "C" {
 #define TFSPH_E_CUDA          4  /* a CUDA runtime call failed */
 #define TFSPH_E_OOM           5  /* device or host allocation failed */
 #define TFSPH_E_INTERNAL      6  /* a device-side consistency check failed */
+#define TFSPH_E_TIMEOUT       7  /* a bounded device-side wait ran out (batched persistent step) */
 
 #define TFSPH_MEM_HOST   0
 #define TFSPH_MEM_DEVICE 1
@@ -269,6 +270,97 @@ int tfsph_version(void);
  * in tfsph_last_error(NULL). */
 int tfsph_cell_ranges_noalloc(const uint32_t *keys, int64_t n, uint32_t n_cells, uint32_t *starts,
                               void *stream);
+
+/* ------------------------------------------------------------------------
+ * Batched ensembles: many independent instances of the step (Sec. 2.3) in
+ * one context, each with its own box, particle counts, h, cell grid,
+ * masses, sound speed, t_stop values, tau and g. All instances share dim,
+ * tstar_mode and cell_acc, and the batch runs FP32 state (precision must be
+ * TFSPH_FP32). Each instance computes exactly what a single context with
+ * its parameters computes; only the order in which neighbour terms are
+ * summed may differ (rounding).
+ *
+ * A step of the whole batch is replayed from a captured CUDA graph in one of
+ * two launch forms:
+ *   TFSPH_BATCH_PERSISTENT: one cooperative launch per step; its phases are
+ *     separated by grid barriers whose waits are bounded (a wait that runs
+ *     out makes the next tfsph_batch_sync return TFSPH_E_TIMEOUT; the
+ *     context stays usable);
+ *   TFSPH_BATCH_KERNELS: one launch per phase (the default).
+ * tfsph_batch_autotune times the forms and CTA sizes on the current state
+ * (which it restores) and keeps the fastest.
+ * ---------------------------------------------------------------------- */
+typedef struct tfsph_batch tfsph_batch;
+
+#define TFSPH_BATCH_KERNELS    0
+#define TFSPH_BATCH_PERSISTENT 1
+
+typedef struct {
+    int32_t n_inst, dim;
+    int64_t n_gas, n_dust;   /* totals over the instances */
+    int64_t n_cells;         /* total cells (instance grids concatenated) */
+    int32_t mode;            /* TFSPH_BATCH_* */
+    int32_t block;           /* threads per CTA */
+    int32_t grid;            /* CTAs of the persistent launch (0 otherwise) */
+    int32_t graph;           /* 1 when steps replay a captured CUDA graph */
+    int64_t steps;           /* steps taken since init */
+    int64_t launches;        /* kernel launches of those steps (graph kernel nodes count) */
+    int64_t device_bytes;    /* device memory held */
+} tfsph_batch_info_t;
+
+/* Creates a batch of n_inst instances. params[i], n_gas[i], n_dust[i]
+ * describe instance i (each is checked like tfsph_init's). gas and dust list
+ * the same component arrays as tfsph_init, each holding every instance's
+ * particles concatenated in instance order (instance i's gas occupies
+ * [sum_{k<i} n_gas[k], sum_{k<=i} n_gas[k])); the energy array is present
+ * when any instance is adiabatic. frozen (nullable) flags wall gas particles
+ * in the same concatenated order. The particle ids of field exports follow
+ * the concatenated order. Errors: INVALID_ARG, NONFINITE, OUT_OF_DOMAIN,
+ * OOM, CUDA; the message is in tfsph_batch_last_error(NULL). */
+int tfsph_batch_init(tfsph_batch **out, const tfsph_params *params, const int64_t *n_gas, const int64_t *n_dust,
+                     int32_t n_inst, const void *const *gas, const void *const *dust, const uint8_t *frozen,
+                     int mem_kind);
+
+/* Work goes on this stream (cudaStream_t; NULL = legacy default stream). */
+int tfsph_batch_set_stream(tfsph_batch *b, void *stream);
+
+/* Advances every instance by nsteps steps. tau: n_inst host values (> 0),
+ * required on the first call, NULL keeps the previous ones; g: 3 * n_inst
+ * host values (instance-major, components beyond dim ignored), NULL keeps
+ * the previous ones (initially 0). Asynchronous, except that a changed tau
+ * or g is uploaded before the call returns. nsteps = 0 only sets tau, g. */
+int tfsph_batch_step(tfsph_batch *b, const double *tau, const double *g, int32_t nsteps);
+
+/* Selects the launch form: mode TFSPH_BATCH_*, block in {128, 256, 512}
+ * threads per CTA, blocks_per_sm in [1, 16] (persistent form: CTAs per SM,
+ * capped by what fits), barrier_timeout_ms >= 0 (how long a persistent grid
+ * barrier waits before it gives up). */
+int tfsph_batch_config(tfsph_batch *b, int32_t mode, int32_t block, int32_t blocks_per_sm, double barrier_timeout_ms);
+
+/* Times every launch form for `steps` steps from the current state (after
+ * one warm-up step each), restores the state and keeps the fastest; returns
+ * its mode, block, blocks_per_sm and time per step (any output may be
+ * NULL). Synchronises. tau must have been set. */
+int tfsph_batch_autotune(tfsph_batch *b, int32_t steps, int32_t *mode, int32_t *block, int32_t *blocks_per_sm,
+                         float *ms_per_step);
+
+/* Copies one field of every instance, concatenated in instance order and
+ * in input order inside each instance (TFSPH_FIELD_POS_G, VEL_G, ENERGY_G,
+ * RHO_G, POS_D, VEL_D, TSTOP_D; RHO_G bins the current state first). Host
+ * copies synchronise. */
+int tfsph_batch_fields(tfsph_batch *b, int field, void *out, int mem_kind);
+
+int tfsph_batch_info(const tfsph_batch *b, tfsph_batch_info_t *out);
+
+/* Waits for the batch's work and reports device-side errors (TIMEOUT,
+ * INTERNAL), clearing them. */
+int tfsph_batch_sync(tfsph_batch *b);
+
+/* Message of the last failed call on b (b = NULL: of the last failed
+ * tfsph_batch_init on this thread). */
+const char *tfsph_batch_last_error(const tfsph_batch *b);
+
+void tfsph_batch_destroy(tfsph_batch *b);
 
 #ifdef __cplusplus
 }

@@ -20,7 +20,8 @@ LIB_PATH = os.path.join(_HERE, "libtfsph.so")
 
 # constants mirrored from include/tfsph.h
 TFSPH_OK, TFSPH_E_INVALID_ARG, TFSPH_E_NONFINITE, TFSPH_E_OUT_OF_DOMAIN = 0, 1, 2, 3
-TFSPH_E_CUDA, TFSPH_E_OOM, TFSPH_E_INTERNAL = 4, 5, 6
+TFSPH_E_CUDA, TFSPH_E_OOM, TFSPH_E_INTERNAL, TFSPH_E_TIMEOUT = 4, 5, 6, 7
+TFSPH_BATCH_KERNELS, TFSPH_BATCH_PERSISTENT = 0, 1
 TFSPH_MEM_HOST, TFSPH_MEM_DEVICE = 0, 1
 TFSPH_FP32, TFSPH_FP64 = 0, 1
 TFSPH_EOS_ISOTHERMAL, TFSPH_EOS_ADIABATIC = 0, 1
@@ -52,6 +53,14 @@ class tfsph_info_t(C.Structure):
         ("n_gas", C.c_int64), ("n_dust", C.c_int64), ("n_cells", C.c_int32 * 3), ("reach", C.c_int32 * 3),
         ("n_cells_total", C.c_int64), ("steps", C.c_int64), ("device_bytes", C.c_int64),
         ("launches", C.c_int64),
+    ]
+
+
+class tfsph_batch_info_t(C.Structure):
+    _fields_ = [
+        ("n_inst", C.c_int32), ("dim", C.c_int32), ("n_gas", C.c_int64), ("n_dust", C.c_int64),
+        ("n_cells", C.c_int64), ("mode", C.c_int32), ("block", C.c_int32), ("grid", C.c_int32),
+        ("graph", C.c_int32), ("steps", C.c_int64), ("launches", C.c_int64), ("device_bytes", C.c_int64),
     ]
 
 
@@ -105,6 +114,22 @@ def load() -> C.CDLL:
     lib.tfsph_destroy.argtypes = [ctxp]
     lib.tfsph_destroy.restype = None
     lib.tfsph_version.argtypes = []
+    bp = C.c_void_p
+    lib.tfsph_batch_init.argtypes = [C.POINTER(bp), vp, vp, vp, C.c_int32, vp, vp, vp, i32]
+    lib.tfsph_batch_set_stream.argtypes = [bp, vp]
+    lib.tfsph_batch_step.argtypes = [bp, vp, vp, C.c_int32]
+    lib.tfsph_batch_config.argtypes = [bp, C.c_int32, C.c_int32, C.c_int32, d]
+    lib.tfsph_batch_autotune.argtypes = [bp, C.c_int32, vp, vp, vp, vp]
+    lib.tfsph_batch_fields.argtypes = [bp, i32, vp, i32]
+    lib.tfsph_batch_info.argtypes = [bp, C.POINTER(tfsph_batch_info_t)]
+    lib.tfsph_batch_sync.argtypes = [bp]
+    lib.tfsph_batch_last_error.argtypes = [bp]
+    lib.tfsph_batch_last_error.restype = C.c_char_p
+    lib.tfsph_batch_destroy.argtypes = [bp]
+    lib.tfsph_batch_destroy.restype = None
+    for name in ("tfsph_batch_init", "tfsph_batch_set_stream", "tfsph_batch_step", "tfsph_batch_config",
+                 "tfsph_batch_autotune", "tfsph_batch_fields", "tfsph_batch_info", "tfsph_batch_sync"):
+        getattr(lib, name).restype = C.c_int
     for name in ("tfsph_init", "tfsph_set_state", "tfsph_set_stream", "tfsph_step", "tfsph_step_adjoint", "tfsph_max_dt",
                  "tfsph_fields", "tfsph_debug", "tfsph_info", "tfsph_sync", "tfsph_version",
                  "tfsph_profile", "tfsph_profile_read", "tfsph_cell_ranges_noalloc", "tfsph_state_bytes",
@@ -220,6 +245,67 @@ def tfsph_destroy(ctx) -> None:
 
 def tfsph_version() -> int:
     return load().tfsph_version()
+
+
+def tfsph_batch_init(params_list, n_gas, n_dust, gas_ptrs, dust_ptrs, frozen_ptr, mem_kind: int):
+    """Returns (status, batch handle)."""
+    lib = load()
+    b = C.c_void_p()
+    n = len(params_list)
+    pa = (tfsph_params * n)(*params_list)
+    ng = (C.c_int64 * n)(*[int(x) for x in n_gas])
+    nd = (C.c_int64 * n)(*[int(x) for x in n_dust])
+    ga = (C.c_void_p * max(1, len(gas_ptrs)))(*gas_ptrs)
+    da = (C.c_void_p * max(1, len(dust_ptrs)))(*dust_ptrs)
+    rc = lib.tfsph_batch_init(C.byref(b), C.cast(pa, C.c_void_p), C.cast(ng, C.c_void_p), C.cast(nd, C.c_void_p),
+                              n, C.cast(ga, C.c_void_p), C.cast(da, C.c_void_p), frozen_ptr, int(mem_kind))
+    return rc, b
+
+
+def tfsph_batch_set_stream(b, stream_ptr) -> int:
+    return load().tfsph_batch_set_stream(b, stream_ptr)
+
+
+def tfsph_batch_step(b, tau, g, nsteps: int) -> int:
+    ta = None if tau is None else (C.c_double * len(tau))(*[float(x) for x in tau])
+    ga = None if g is None else (C.c_double * len(g))(*[float(x) for x in g])
+    return load().tfsph_batch_step(b, None if ta is None else C.cast(ta, C.c_void_p),
+                                   None if ga is None else C.cast(ga, C.c_void_p), int(nsteps))
+
+
+def tfsph_batch_config(b, mode: int, block: int, blocks_per_sm: int, barrier_timeout_ms: float) -> int:
+    return load().tfsph_batch_config(b, int(mode), int(block), int(blocks_per_sm), float(barrier_timeout_ms))
+
+
+def tfsph_batch_autotune(b, steps: int):
+    """Returns (status, mode, block, blocks_per_sm, ms per step)."""
+    m, blk, bps, ms = C.c_int32(0), C.c_int32(0), C.c_int32(0), C.c_float(0)
+    rc = load().tfsph_batch_autotune(b, int(steps), C.cast(C.pointer(m), C.c_void_p), C.cast(C.pointer(blk), C.c_void_p),
+                                     C.cast(C.pointer(bps), C.c_void_p), C.cast(C.pointer(ms), C.c_void_p))
+    return rc, m.value, blk.value, bps.value, ms.value
+
+
+def tfsph_batch_fields(b, field: int, out_ptr, mem_kind: int) -> int:
+    return load().tfsph_batch_fields(b, int(field), out_ptr, int(mem_kind))
+
+
+def tfsph_batch_info(b):
+    info = tfsph_batch_info_t()
+    rc = load().tfsph_batch_info(b, C.byref(info))
+    return rc, info
+
+
+def tfsph_batch_sync(b) -> int:
+    return load().tfsph_batch_sync(b)
+
+
+def tfsph_batch_last_error(b) -> str:
+    s = load().tfsph_batch_last_error(b)
+    return s.decode() if s else ""
+
+
+def tfsph_batch_destroy(b) -> None:
+    load().tfsph_batch_destroy(b)
 
 
 # ---------------------------------------------------------------------------
@@ -406,6 +492,111 @@ class Context:
         if getattr(self, "ctx", None):
             tfsph_destroy(self.ctx)
             self.ctx = None
+
+    def __enter__(self):
+        return self
+
+    def __exit__(self, *exc):
+        self.close()
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+
+def _bcheck(rc: int, b=None):
+    if rc != TFSPH_OK:
+        raise TfsphError(rc, tfsph_batch_last_error(b))
+
+
+class Batch:
+    """A batch of independent instances (FP32 state). ``instances`` is a list
+    of (params, gx, gv, dx, du, tstop[, frozen]) with numpy arrays of shape
+    (dim, n) (tstop, frozen: (n,)); they are concatenated in list order."""
+
+    def __init__(self, instances, stream=None):
+        import numpy as _np
+        params = [it[0] for it in instances]
+        self.dim = int(params[0].dim)
+        d = self.dim
+        self.n_gas = [int(it[1].shape[-1]) for it in instances]
+        self.n_dust = [int(it[3].shape[-1]) for it in instances]
+        cat = lambda idx, k: _np.ascontiguousarray(
+            _np.concatenate([_np.asarray(it[idx], dtype=_np.float32)[k] for it in instances]))
+        gas = [cat(1, k) for k in range(d)] + [cat(2, k) for k in range(d)]
+        dust = [cat(3, k) for k in range(d)] + [cat(4, k) for k in range(d)]
+        dust.append(_np.ascontiguousarray(_np.concatenate([_np.asarray(it[5], dtype=_np.float32)
+                                                           for it in instances])))
+        has_fz = any(len(it) > 6 and it[6] is not None for it in instances)
+        fz = None
+        if has_fz:
+            fz = _np.ascontiguousarray(_np.concatenate([
+                _np.asarray(it[6], dtype=_np.uint8) if len(it) > 6 and it[6] is not None
+                else _np.zeros(int(it[1].shape[-1]), _np.uint8) for it in instances]))
+        keep = gas + dust + ([fz] if fz is not None else [])
+        rc, self.b = tfsph_batch_init(params, self.n_gas, self.n_dust, [a.ctypes.data for a in gas],
+                                      [a.ctypes.data for a in dust], None if fz is None else fz.ctypes.data,
+                                      TFSPH_MEM_HOST)
+        del keep
+        if rc != TFSPH_OK:
+            self.b = None
+            raise TfsphError(rc, tfsph_batch_last_error(None))
+        self.n_inst = len(instances)
+        self.goff = _np.concatenate([[0], _np.cumsum(self.n_gas)]).astype(_np.int64)
+        self.doff = _np.concatenate([[0], _np.cumsum(self.n_dust)]).astype(_np.int64)
+        if stream is not None:
+            self.set_stream(stream)
+
+    def set_stream(self, stream):
+        handle = getattr(stream, "cuda_stream", stream)
+        _bcheck(tfsph_batch_set_stream(self.b, C.c_void_p(int(handle) if handle else 0)), self.b)
+
+    def step(self, tau=None, g=None, nsteps: int = 1):
+        gflat = None
+        if g is not None:
+            gflat = np.zeros(3 * self.n_inst)
+            ga = np.asarray(g, dtype=np.float64).reshape(self.n_inst, -1)
+            gflat.reshape(self.n_inst, 3)[:, :ga.shape[1]] = ga
+        _bcheck(tfsph_batch_step(self.b, None if tau is None else list(np.broadcast_to(
+            np.asarray(tau, dtype=np.float64), (self.n_inst,))), gflat, nsteps), self.b)
+
+    def config(self, mode: int, block: int = 256, blocks_per_sm: int = 1, barrier_timeout_ms: float = 2000.0):
+        _bcheck(tfsph_batch_config(self.b, mode, block, blocks_per_sm, barrier_timeout_ms), self.b)
+
+    def autotune(self, steps: int = 5):
+        rc, mode, block, bps, ms = tfsph_batch_autotune(self.b, steps)
+        _bcheck(rc, self.b)
+        return {"mode": mode, "block": block, "blocks_per_sm": bps, "ms_per_step": ms}
+
+    def field(self, field: int):
+        vec = field in (TFSPH_FIELD_POS_G, TFSPH_FIELD_VEL_G, TFSPH_FIELD_POS_D, TFSPH_FIELD_VEL_D)
+        gas = field in (TFSPH_FIELD_POS_G, TFSPH_FIELD_VEL_G, TFSPH_FIELD_ENERGY_G, TFSPH_FIELD_RHO_G)
+        n = int(self.goff[-1] if gas else self.doff[-1])
+        out = np.zeros((self.dim, n) if vec else (n,), dtype=np.float32)
+        _bcheck(tfsph_batch_fields(self.b, field, out.ctypes.data, TFSPH_MEM_HOST), self.b)
+        return out
+
+    def instance_field(self, field: int, i: int):
+        """The field of instance i (a view of one export)."""
+        a = self.field(field)
+        gas = field in (TFSPH_FIELD_POS_G, TFSPH_FIELD_VEL_G, TFSPH_FIELD_ENERGY_G, TFSPH_FIELD_RHO_G)
+        off = self.goff if gas else self.doff
+        return a[..., off[i]:off[i + 1]]
+
+    def info(self) -> tfsph_batch_info_t:
+        rc, info = tfsph_batch_info(self.b)
+        _bcheck(rc, self.b)
+        return info
+
+    def sync(self):
+        _bcheck(tfsph_batch_sync(self.b), self.b)
+
+    def close(self):
+        if getattr(self, "b", None):
+            tfsph_batch_destroy(self.b)
+            self.b = None
 
     def __enter__(self):
         return self

@@ -13,7 +13,7 @@
 //                state is copied there (double buffer).
 // Also: packing of user arrays, field export, t_stop updates, input checks
 // and the Courant speed reduction.
-#include "tfsph_internal.cuh"
+#include "sort_ops.cuh"
 
 namespace tfsph {
 namespace {
@@ -126,25 +126,6 @@ k_scan_down(const uint32_t *__restrict__ cg, const uint32_t *__restrict__ cd, ui
     if (blockIdx.x == 0 && threadIdx.x == 0) st[ncells] = blockIdx.y == 0 ? ng : nd;
 }
 
-// Takes one slot of cell k; a count that is already zero or a slot past the
-// end means the counts and keys disagree: flagged, nothing written.
-__device__ __forceinline__ void scatter_one(uint32_t i, const uint32_t *__restrict__ key,
-                                            const uint32_t *__restrict__ id, uint32_t *__restrict__ cnt,
-                                            const uint32_t *__restrict__ start, uint32_t *__restrict__ src,
-                                            uint32_t *__restrict__ tid, uint32_t n, int *err)
-{
-    const uint32_t k = key[i];
-    const uint32_t old = atomicSub(&cnt[k], 1u);
-    const uint32_t slot = start[k] + old - 1u;
-    if (old == 0u || slot >= n) {
-        atomicAdd(&cnt[k], 1u);
-        atomicOr(err, kErrInternal);
-        return;
-    }
-    src[slot] = i;
-    tid[slot] = id[i] & kIdMask;
-}
-
 __global__ void k_scatter(const uint32_t *__restrict__ kg, const uint32_t *__restrict__ idg,
                           uint32_t *__restrict__ cg, const uint32_t *__restrict__ sg, uint32_t *__restrict__ srcg,
                           uint32_t *__restrict__ tidg, int ng, const uint32_t *__restrict__ kd,
@@ -155,35 +136,6 @@ __global__ void k_scatter(const uint32_t *__restrict__ kg, const uint32_t *__res
     const int i = blockIdx.x * blockDim.x + threadIdx.x;
     if (i < ng) scatter_one((uint32_t)i, kg, idg, cg, sg, srcg, tidg, (uint32_t)ng, err);
     else if (i < ng + nd) scatter_one((uint32_t)(i - ng), kd, idd, cd, sd, srcd, tidd, (uint32_t)nd, err);
-}
-
-template <class T>
-__device__ __forceinline__ void rank_move(uint32_t s, const uint32_t *__restrict__ key,
-                                          const uint32_t *__restrict__ start, const uint32_t *__restrict__ src,
-                                          const uint32_t *__restrict__ tid, const V4<T> *__restrict__ pos,
-                                          const V4<T> *__restrict__ vel, const uint32_t *__restrict__ id,
-                                          V4<T> *__restrict__ opos, V4<T> *__restrict__ ovel,
-                                          uint32_t *__restrict__ oid, uint32_t n, int *err)
-{
-    const uint32_t i = src[s];
-    if (i >= n) {  // a slot the scatter did not fill (flagged there too)
-        atomicOr(err, kErrInternal);
-        return;
-    }
-    const uint32_t k = key[i];
-    const uint32_t b = start[k], e = start[k + 1];
-    uint32_t d = b;
-    if (e - b > 1) {
-        const uint32_t mine = tid[s];
-        for (uint32_t t = b; t < e; ++t) d += tid[t] < mine ? 1u : 0u;
-    }
-    if (d >= e) {
-        atomicOr(err, kErrInternal);
-        return;
-    }
-    opos[d] = pos[i];
-    ovel[d] = vel[i];
-    oid[d] = id[i];
 }
 
 template <class T>

@@ -20,7 +20,7 @@
 //     next cell key.
 // The per-cell results live in shared memory only; nothing per cell is
 // written to global memory.
-#include "tfsph_internal.cuh"
+#include "drag_ops.cuh"
 
 namespace tfsph {
 namespace {
@@ -47,47 +47,17 @@ k_cell_update(Geo<T> G, Phys<T> Ph, A tau, A g0, A g1, A g2, int harmonic, int h
     // ---- phase 1: per-cell sums and the implicit solve ----
     int drag = 0;
     if (c < ncells) {
-        const uint32_t gs = gstart[c], ge = gstart[c + 1];
-        const uint32_t ds = dstart[c], de = dstart[c + 1];
-        A N = A(0), L = A(0), st = A(0);
-        A sv[3] = {A(0), A(0), A(0)}, sa[3] = {A(0), A(0), A(0)}, su[3] = {A(0), A(0), A(0)};
-        for (uint32_t a = gs; a < ge; ++a) {
-            if (has_frozen && (gid[a] & kFrozenBit)) continue;
-            const V4<T> v = gvel[a];
-            const V4<T> ac = acc[a];
-            N += A(1);
-            sv[0] += A(v.x);
-            sa[0] += A(ac.x);
-            if (DIM > 1) { sv[1] += A(v.y); sa[1] += A(ac.y); }
-            if (DIM > 2) { sv[2] += A(v.z); sa[2] += A(ac.z); }
-        }
-        for (uint32_t j = ds; j < de; ++j) {
-            const V4<T> u = dvel[j];
-            L += A(1);
-            su[0] += A(u.x);
-            if (DIM > 1) su[1] += A(u.y);
-            if (DIM > 2) su[2] += A(u.z);
-            st += harmonic ? A(1) / A(u.w) : A(u.w);
-        }
-        drag = (N > A(0) && L > A(0)) ? 1 : 0;
+        T un[3] = {T(0), T(0), T(0)}, vn[3] = {T(0), T(0), T(0)}, ig = T(0), id = T(0);
+        drag = cell_drag_solve<T, A, DIM>(Ph, tau, gv, harmonic, has_frozen, gvel, gid, acc, gstart[c],
+                                          gstart[c + 1], dvel, dstart[c], dstart[c + 1], un, vn, ig, id);
         if (drag) {
-            const A eps = A(Ph.m_d) * L / (A(Ph.m_g) * N);
-            const A tst = harmonic ? L / st : st / L;
-            const A rt = tau / tst;
-            const A den = A(1) + rt * (A(1) + eps);
-            const A invN = A(1) / N, invL = A(1) / L;
 #pragma unroll
             for (int k = 0; k < DIM; ++k) {
-                const A vs = sv[k] * invN;
-                const A us = su[k] * invL;
-                const A ab = sa[k] * invN;
-                const A wn = ((vs - us) + tau * ab) / den;
-                const A un = us + tau * gv[k] + rt * wn;
-                s_us[k][threadIdx.x] = T(un);
-                s_vs[k][threadIdx.x] = T(un + wn);
+                s_us[k][threadIdx.x] = un[k];
+                s_vs[k][threadIdx.x] = vn[k];
             }
-            s_ig[threadIdx.x] = T(A(1) / (A(1) + rt * eps));
-            s_id[threadIdx.x] = T(A(1) / (A(1) + rt));
+            s_ig[threadIdx.x] = ig;
+            s_id[threadIdx.x] = id;
         }
     }
     s_drag[threadIdx.x] = drag;
@@ -108,33 +78,14 @@ k_cell_update(Geo<T> G, Phys<T> Ph, A tau, A g0, A g1, A g2, int harmonic, int h
             V4<T> v = gvel[a];
             const V4<T> ac = acc[a];
             const uint32_t lc = cell_key<T, DIM>(G, p.x, p.y, p.z) - c0;
-            T vn[3];
-            vn[0] = v.x + tau_t * (ac.x + gt[0]);
-            vn[1] = DIM > 1 ? v.y + tau_t * (ac.y + gt[1]) : T(0);
-            vn[2] = DIM > 2 ? v.z + tau_t * (ac.z + gt[2]) : T(0);
-            if (lc < (uint32_t)kCellsPerCta && s_drag[lc]) {
-                const T ig = s_ig[lc];
+            const bool dr = lc < (uint32_t)kCellsPerCta && s_drag[lc];
+            T us[3] = {T(0), T(0), T(0)}, ig = T(0);
+            if (dr) {
+                ig = s_ig[lc];
 #pragma unroll
-                for (int k = 0; k < DIM; ++k) {
-                    const T us = s_us[k][lc];
-                    vn[k] = us + (vn[k] - us) * ig;
-                }
+                for (int k = 0; k < DIM; ++k) us[k] = s_us[k][lc];
             }
-            v.x = vn[0];
-            p.x = p.x + tau_t * vn[0];
-            if (G.per[0]) p.x = wrap_periodic(p.x, G.lo[0], G.L[0]);
-            if (DIM > 1) {
-                v.y = vn[1];
-                p.y = p.y + tau_t * vn[1];
-                if (G.per[1]) p.y = wrap_periodic(p.y, G.lo[1], G.L[1]);
-            }
-            if (DIM > 2) {
-                v.z = vn[2];
-                p.z = p.z + tau_t * vn[2];
-                if (G.per[2]) p.z = wrap_periodic(p.z, G.lo[2], G.L[2]);
-            }
-            if (adiabatic) v.w = v.w + tau_t * ac.w;
-            p.w = T(0);
+            gas_particle_update<T, DIM>(G, tau_t, gt, adiabatic, p, v, ac, dr, us, ig);
             gpos[a] = p;
             gvel[a] = v;
             gkey[a] = cell_key<T, DIM>(G, p.x, p.y, p.z);
@@ -146,31 +97,14 @@ k_cell_update(Geo<T> G, Phys<T> Ph, A tau, A g0, A g1, A g2, int harmonic, int h
             V4<T> p = dpos[j];
             V4<T> u = dvel[j];
             const uint32_t lc = cell_key<T, DIM>(G, p.x, p.y, p.z) - c0;
-            T un[3];
-            un[0] = u.x + tau_t * gt[0];
-            un[1] = DIM > 1 ? u.y + tau_t * gt[1] : T(0);
-            un[2] = DIM > 2 ? u.z + tau_t * gt[2] : T(0);
-            if (lc < (uint32_t)kCellsPerCta && s_drag[lc]) {
-                const T id = s_id[lc];
+            const bool dr = lc < (uint32_t)kCellsPerCta && s_drag[lc];
+            T vs[3] = {T(0), T(0), T(0)}, id = T(0);
+            if (dr) {
+                id = s_id[lc];
 #pragma unroll
-                for (int k = 0; k < DIM; ++k) {
-                    const T vs = s_vs[k][lc];
-                    un[k] = vs + (un[k] - vs) * id;
-                }
+                for (int k = 0; k < DIM; ++k) vs[k] = s_vs[k][lc];
             }
-            u.x = un[0];
-            p.x = p.x + tau_t * un[0];
-            if (G.per[0]) p.x = wrap_periodic(p.x, G.lo[0], G.L[0]);
-            if (DIM > 1) {
-                u.y = un[1];
-                p.y = p.y + tau_t * un[1];
-                if (G.per[1]) p.y = wrap_periodic(p.y, G.lo[1], G.L[1]);
-            }
-            if (DIM > 2) {
-                u.z = un[2];
-                p.z = p.z + tau_t * un[2];
-                if (G.per[2]) p.z = wrap_periodic(p.z, G.lo[2], G.L[2]);
-            }
+            dust_particle_update<T, DIM>(G, tau_t, gt, p, u, dr, vs, id);
             dpos[j] = p;
             dvel[j] = u;
             dkey[j] = cell_key<T, DIM>(G, p.x, p.y, p.z);

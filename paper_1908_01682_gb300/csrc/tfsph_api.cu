@@ -105,64 +105,11 @@ int dalloc(tfsph_ctx *c, void **out, size_t bytes)
 
 template <class T> void build_geo(tfsph_ctx *c)
 {
-    const tfsph_params &p = c->p;
     Geo<T> G{};
-    G.dim = p.dim;
-    const double u = sizeof(T) == 4 ? 0x1p-24 : 0x1p-53;
-    double span = 0.0;
-    for (int d = 0; d < p.dim; ++d) span = fmax(span, fmax(fabs(p.lo[d]), fabs(p.hi[d])) + (p.hi[d] - p.lo[d]));
-    const double margin = 8.0 * u * span + 16.0 * u * 2.0 * p.h;
-    const double reach = 2.0 * p.h + margin;
-    for (int d = 0; d < 3; ++d) {
-        if (d >= p.dim) {
-            G.n[d] = 1;
-            G.R[d] = 0;
-            G.per[d] = 0;
-            G.full[d] = 0;
-            G.lo[d] = T(0);
-            G.inv_w[d] = T(0);
-            G.w[d] = T(1);
-            G.L[d] = T(1);
-            G.halfL[d] = T(0.5);
-            continue;
-        }
-        const double L = p.hi[d] - p.lo[d];
-        const int n = c->ncell[d];
-        const double w = L / (double)n;
-        G.n[d] = n;
-        G.R[d] = (int)floor(reach / w) + 1;
-        G.per[d] = p.periodic[d] ? 1 : 0;
-        G.full[d] = (G.per[d] && 2 * G.R[d] + 1 >= n) ? 1 : 0;
-        G.lo[d] = T(p.lo[d]);
-        G.inv_w[d] = T((double)n / L);
-        G.w[d] = T(w);
-        G.L[d] = T(L);
-        G.halfL[d] = T(0.5 * L);
-        c->reach[d] = G.R[d];
-    }
-    G.h2x4 = T(4.0 * p.h * p.h);
-    G.lim2 = T(reach * reach * (1.0 + 16.0 * u));
-    const double sigma = p.dim == 1 ? 2.0 / 3.0 : (p.dim == 2 ? 10.0 / (7.0 * M_PI) : 1.0 / M_PI);
-    G.wnorm = T(sigma / pow(p.h, p.dim));
-    G.fnorm = T(sigma / pow(p.h, p.dim + 2));
-    G.inv_h = T(1.0 / p.h);
-    G.h = T(p.h);
-    G.ncells = c->ncells;
-    memcpy(c->geo, &G, sizeof(G));
-
     Phys<T> Ph{};
-    Ph.m_g = T(p.m_gas);
-    Ph.m_d = T(p.m_dust);
-    Ph.cs = T(p.cs);
-    Ph.cs2 = T(p.cs * p.cs);
-    Ph.gm1 = T(p.gamma - 1.0);
-    Ph.gamma = T(p.gamma);
-    Ph.av_alpha = T(p.av_alpha);
-    Ph.av_beta = T(p.av_beta);
-    Ph.eta2 = T(0.01 * p.h * p.h);
-    Ph.h = T(p.h);
-    Ph.eos = p.eos;
-    Ph.av = (p.av_alpha > 0.0 || p.av_beta > 0.0) ? 1 : 0;
+    make_geo_phys<T>(c->p, c->ncell, c->ncells, G, Ph);
+    for (int d = 0; d < 3; ++d) c->reach[d] = G.R[d];
+    memcpy(c->geo, &G, sizeof(G));
     memcpy(c->phys, &Ph, sizeof(Ph));
 }
 
@@ -175,42 +122,6 @@ LaunchCtx lctx(const tfsph_ctx *c)
     L.d_err = c->d_err;
     L.ev = nullptr;
     return L;
-}
-
-int validate_params(const tfsph_params *p, int64_t ng, int64_t nd, std::string &why)
-{
-    char buf[256];
-    if (!p) { why = "params is NULL"; return TFSPH_E_INVALID_ARG; }
-    if (p->dim < 1 || p->dim > 3) { why = "dim must be 1, 2 or 3"; return TFSPH_E_INVALID_ARG; }
-    if (p->precision != TFSPH_FP32 && p->precision != TFSPH_FP64) { why = "unknown precision"; return TFSPH_E_INVALID_ARG; }
-    if (p->kernel != TFSPH_KERNEL_CUBIC) { why = "unknown kernel"; return TFSPH_E_INVALID_ARG; }
-    if (p->eos != TFSPH_EOS_ISOTHERMAL && p->eos != TFSPH_EOS_ADIABATIC) { why = "unknown eos"; return TFSPH_E_INVALID_ARG; }
-    if (p->tstar_mode != TFSPH_TSTAR_ARITHMETIC && p->tstar_mode != TFSPH_TSTAR_HARMONIC) { why = "unknown tstar_mode"; return TFSPH_E_INVALID_ARG; }
-    if (p->cell_acc != TFSPH_CELL_ACC_FP32 && p->cell_acc != TFSPH_CELL_ACC_FP64) { why = "unknown cell_acc"; return TFSPH_E_INVALID_ARG; }
-    if (p->reserved != 0) { why = "reserved must be 0"; return TFSPH_E_INVALID_ARG; }
-    const double vals[] = {p->h, p->cell_size, p->m_gas, p->m_dust, p->cs, p->gamma, p->av_alpha, p->av_beta};
-    for (double v : vals)
-        if (!std::isfinite(v)) { why = "non-finite parameter"; return TFSPH_E_NONFINITE; }
-    if (!(p->h > 0) || !(p->cell_size > 0)) { why = "h and cell_size must be > 0"; return TFSPH_E_INVALID_ARG; }
-    if (!(p->m_gas > 0) || !(p->m_dust > 0)) { why = "particle masses must be > 0"; return TFSPH_E_INVALID_ARG; }
-    if (!(p->cs > 0)) { why = "cs must be > 0"; return TFSPH_E_INVALID_ARG; }
-    if (p->eos == TFSPH_EOS_ADIABATIC && !(p->gamma > 1.0)) { why = "gamma must be > 1"; return TFSPH_E_INVALID_ARG; }
-    if (p->av_alpha < 0 || p->av_beta < 0) { why = "viscosity coefficients must be >= 0"; return TFSPH_E_INVALID_ARG; }
-    if (ng < 0 || nd < 0 || ng >= (int64_t)1 << 31 || nd >= (int64_t)1 << 31) { why = "particle counts must be in [0, 2^31)"; return TFSPH_E_INVALID_ARG; }
-    double ncells = 1.0;
-    for (int d = 0; d < p->dim; ++d) {
-        if (!std::isfinite(p->lo[d]) || !std::isfinite(p->hi[d])) { why = "non-finite box"; return TFSPH_E_NONFINITE; }
-        const double L = p->hi[d] - p->lo[d];
-        if (!(L > 0)) { why = "box must have hi > lo"; return TFSPH_E_INVALID_ARG; }
-        if (p->periodic[d] && L < 4.0 * p->h) {
-            snprintf(buf, sizeof buf, "periodic axis %d is shorter than 4h (%g < %g)", d, L, 4.0 * p->h);
-            why = buf;
-            return TFSPH_E_INVALID_ARG;
-        }
-        ncells *= fmax(1.0, floor(L / p->cell_size));
-    }
-    if (ncells > 1.0e9) { why = "too many cells (> 1e9); increase cell_size"; return TFSPH_E_INVALID_ARG; }
-    return TFSPH_OK;
 }
 
 // Device copies of user arrays: returns device pointers (host input is staged).
@@ -402,6 +313,7 @@ const char *tfsph_status_string(int code)
         case TFSPH_E_CUDA: return "TFSPH_E_CUDA";
         case TFSPH_E_OOM: return "TFSPH_E_OOM";
         case TFSPH_E_INTERNAL: return "TFSPH_E_INTERNAL";
+        case TFSPH_E_TIMEOUT: return "TFSPH_E_TIMEOUT";
         default: return "TFSPH_E_UNKNOWN";
     }
 }
@@ -436,13 +348,7 @@ int tfsph_init(tfsph_ctx **out, const tfsph_params *p, const void *const *gas, i
     c->dim = p->dim;
     c->cell_acc = p->precision == TFSPH_FP64 ? TFSPH_CELL_ACC_FP64 : p->cell_acc;
     c->tsize = p->precision == TFSPH_FP64 ? 8 : 4;
-    uint64_t nc = 1;
-    for (int d = 0; d < 3; ++d) {
-        if (d < p->dim) c->ncell[d] = (int)fmax(1.0, floor((p->hi[d] - p->lo[d]) / p->cell_size));
-        else c->ncell[d] = 1;
-        nc *= (uint64_t)c->ncell[d];
-    }
-    c->ncells = (uint32_t)nc;
+    c->ncells = cell_grid(*p, c->ncell);
     c->G.n = n_gas;
     c->D.n = n_dust;
     if (p->precision == TFSPH_FP64) build_geo<double>(c);

@@ -17,6 +17,7 @@
 
 #include <cmath>
 #include <cstdint>
+#include <string>
 
 #include "tfsph.h"
 
@@ -28,6 +29,7 @@ constexpr uint32_t kFrozenBit = 0x80000000u;
 // Device error word bits (set by kernels, read by tfsph_sync).
 constexpr int kErrBadTstop = 1;
 constexpr int kErrInternal = 2;
+constexpr int kErrTimeout = 4;   // a bounded device-side wait ran out
 
 struct alignas(32) double4a {
     double x, y, z, w;
@@ -145,6 +147,75 @@ cudaError_t launch_density_adjoint(const LaunchCtx &L, const void *geo, const vo
 
 // tfsph_api.cu: message for tfsph_last_error(NULL) from calls without a context
 void set_unbound_error(const char *msg);
+
+// params.cu: checks of one parameter set with its particle counts (a
+// TFSPH_E_* code, the reason in why), and its cell grid (cells per axis;
+// returns the cell count; validate_params bounds it by 1e9).
+int validate_params(const tfsph_params *p, int64_t ng, int64_t nd, std::string &why);
+uint32_t cell_grid(const tfsph_params &p, int ncell[3]);
+
+// Grid geometry and physical constants of a parameter set, computed in double
+// and rounded once to T. The pruning radius is 2h plus a margin covering the
+// rounding of cell coordinates and of r^2, so no neighbour is ever pruned.
+template <class T>
+void make_geo_phys(const tfsph_params &p, const int ncell[3], uint32_t ncells, Geo<T> &G, Phys<T> &Ph)
+{
+    G = Geo<T>{};
+    G.dim = p.dim;
+    const double u = sizeof(T) == 4 ? 0x1p-24 : 0x1p-53;
+    double span = 0.0;
+    for (int d = 0; d < p.dim; ++d) span = fmax(span, fmax(fabs(p.lo[d]), fabs(p.hi[d])) + (p.hi[d] - p.lo[d]));
+    const double margin = 8.0 * u * span + 16.0 * u * 2.0 * p.h;
+    const double reach = 2.0 * p.h + margin;
+    for (int d = 0; d < 3; ++d) {
+        if (d >= p.dim) {
+            G.n[d] = 1;
+            G.R[d] = 0;
+            G.per[d] = 0;
+            G.full[d] = 0;
+            G.lo[d] = T(0);
+            G.inv_w[d] = T(0);
+            G.w[d] = T(1);
+            G.L[d] = T(1);
+            G.halfL[d] = T(0.5);
+            continue;
+        }
+        const double L = p.hi[d] - p.lo[d];
+        const int n = ncell[d];
+        const double w = L / (double)n;
+        G.n[d] = n;
+        G.R[d] = (int)floor(reach / w) + 1;
+        G.per[d] = p.periodic[d] ? 1 : 0;
+        G.full[d] = (G.per[d] && 2 * G.R[d] + 1 >= n) ? 1 : 0;
+        G.lo[d] = T(p.lo[d]);
+        G.inv_w[d] = T((double)n / L);
+        G.w[d] = T(w);
+        G.L[d] = T(L);
+        G.halfL[d] = T(0.5 * L);
+    }
+    G.h2x4 = T(4.0 * p.h * p.h);
+    G.lim2 = T(reach * reach * (1.0 + 16.0 * u));
+    const double sigma = p.dim == 1 ? 2.0 / 3.0 : (p.dim == 2 ? 10.0 / (7.0 * M_PI) : 1.0 / M_PI);
+    G.wnorm = T(sigma / pow(p.h, p.dim));
+    G.fnorm = T(sigma / pow(p.h, p.dim + 2));
+    G.inv_h = T(1.0 / p.h);
+    G.h = T(p.h);
+    G.ncells = ncells;
+
+    Ph = Phys<T>{};
+    Ph.m_g = T(p.m_gas);
+    Ph.m_d = T(p.m_dust);
+    Ph.cs = T(p.cs);
+    Ph.cs2 = T(p.cs * p.cs);
+    Ph.gm1 = T(p.gamma - 1.0);
+    Ph.gamma = T(p.gamma);
+    Ph.av_alpha = T(p.av_alpha);
+    Ph.av_beta = T(p.av_beta);
+    Ph.eta2 = T(0.01 * p.h * p.h);
+    Ph.h = T(p.h);
+    Ph.eos = p.eos;
+    Ph.av = (p.av_alpha > 0.0 || p.av_beta > 0.0) ? 1 : 0;
+}
 
 // drag.cu
 struct StepArgs {

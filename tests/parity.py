@@ -1,0 +1,94 @@
+"""Element-wise comparison of one GPU step with the FP64 oracle, shared by the
+single-context and batched parity tests.
+
+Within tolerance after one step, tol = 1e-5 (FP32 path) or 1e-12 (FP64 path):
+- densities, positions and energies: normwise ||x - x_ref|| / ||x_ref|| <= tol
+  (the density sums have positive terms only);
+- pressure acceleration and velocities, element by element:
+      |A - A_ref|  <= tol |A_ref| + K u S_a
+      |v' - v'_ref| <= tol (|v'_ref| + |v|) + K u tau (S_a + S_cell)
+  where S_a is the magnitude sum of particle a's pair terms (reported by the
+  oracle), S_cell its mean over the cell's gas, u the unit roundoff of the
+  path (2^-24 or 2^-53) and K = 128.
+"""
+import numpy as np
+
+from conftest import normwise, oracle_params
+
+TOL = {0: 1e-5, 1: 1e-12}
+UNIT = {0: 2.0 ** -24, 1: 2.0 ** -53}
+KAPPA = 128.0
+
+
+def _pos_err(a, ref, w):
+    """Normwise position error with periodic differences taken as minimum images."""
+    d = np.asarray(a) - np.asarray(ref)
+    if d.size == 0:
+        return 0.0
+    for k in range(w.dim):
+        if w.params["periodic"][k]:
+            L = w.params["hi"][k] - w.params["lo"][k]
+            d[k] -= L * np.round(d[k] / L)
+    return float(np.linalg.norm(d)) / max(float(np.linalg.norm(ref)), 1e-300)
+
+
+def _cell_mean(values, keys, ncells, mask=None):
+    """Mean of per-particle values over each cell (0 for empty cells)."""
+    m = np.ones_like(values, dtype=bool) if mask is None else mask
+    s = np.bincount(keys[m], weights=values[m], minlength=ncells)
+    n = np.bincount(keys[m], minlength=ncells)
+    return np.where(n > 0, s / np.maximum(n, 1), 0.0)
+
+
+def _bound_ratio(err, bound):
+    """max over elements of |err| / bound (<= 1 passes)."""
+    err = np.abs(np.asarray(err, np.float64))
+    if err.size == 0:
+        return 0.0
+    return float(np.max(err / np.maximum(bound, 1e-300)))
+
+
+def oracle_step(orc, w, tau=None, g=None, **pover):
+    p = oracle_params(w, **pover)
+    s = orc.make_state(p, w.gx, w.gv, w.dx, w.du, w.tstop, ge=w.ge, frozen=w.frozen)
+    r = orc.step(p, s, w.tau if tau is None else tau, w.g if g is None else g)
+    rho_d, _, _ = orc.density(p, w.dx, p.m_dust) if w.n_dust else (np.zeros(0), None, None)
+    return p, s, r, rho_d
+
+
+def check_one_step(orc, w, gpu, prec, tol=None, tau=None, g=None):
+    """Checks the GPU outputs in ``gpu`` (id order: gx, gv, dx, du; optional
+    rho_g, rho_d before the step, acc_g, ge) against the oracle's step of w.
+    Returns (oracle result, normwise errors)."""
+    tol = TOL[prec] if tol is None else tol
+    ku = KAPPA * UNIT[prec]
+    tau = w.tau if tau is None else tau
+    p, s, r, rho_d = oracle_step(orc, w, tau=tau, g=g)
+    ncells = len(r.cstart_g) - 1
+    moving = np.ones(w.n_gas, bool) if w.frozen is None else w.frozen == 0
+    S = r.acc_scale_g
+    S_cell_g = _cell_mean(S, r.keys_g, ncells, moving) if w.n_gas else np.zeros(ncells)
+    errs = {"gx": _pos_err(gpu["gx"], s.gx, w), "dx": _pos_err(gpu["dx"], s.dx, w)}
+    if "rho_g" in gpu:
+        errs["rho_g"] = normwise(gpu["rho_g"], r.rho_g)
+    if "rho_d" in gpu:
+        errs["rho_d"] = normwise(gpu["rho_d"], rho_d)
+    if w.params["eos"] == 1:
+        errs["ge"] = normwise(gpu["ge"], s.ge)
+    for k, e in errs.items():
+        assert e <= tol, f"{k}: normwise error {e:.3e} > {tol:.0e} ({errs})"
+    ratios = {
+        "gv": _bound_ratio(gpu["gv"][:, moving] - s.gv[:, moving],
+                           tol * (np.abs(s.gv[:, moving]) + np.abs(w.gv[:, moving]))
+                           + ku * tau * (S[moving] + S_cell_g[r.keys_g][moving])),
+        "du": _bound_ratio(gpu["du"] - s.du,
+                           tol * (np.abs(s.du) + np.abs(w.du)) + ku * tau * S_cell_g[r.keys_d]),
+    }
+    if "acc_g" in gpu:
+        ratios["acc_g"] = _bound_ratio(gpu["acc_g"][:, moving] - r.acc_g[:, moving],
+                                       tol * np.abs(r.acc_g[:, moving]) + ku * S[moving])
+    for k, e in ratios.items():
+        assert e <= 1.0, f"{k}: error / bound = {e:.3e} ({ratios}; normwise {errs})"
+    errs["gv_normwise"] = normwise(gpu["gv"], s.gv)
+    errs["du_normwise"] = normwise(gpu["du"], s.du)
+    return r, errs

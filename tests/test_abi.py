@@ -85,3 +85,36 @@ def test_null_context_is_an_error_not_a_crash(lib):
     assert b.tfsph_step(None, 0.1, None, 0, (0, 0, 0)) == b.TFSPH_E_INVALID_ARG
     assert b.tfsph_sync(None) == b.TFSPH_E_INVALID_ARG
     b.tfsph_destroy(None)
+
+
+def _batch_args(b, dims=(1, 1), precision=0, n=4):
+    params = [b.make_params(d, (0.0,) * d, (1.0,) * d, (1,) * d, 0.05, 0.1, 0.1, 0.1, precision=precision)
+              for d in dims]
+    x = np.linspace(0.1, 0.9, n * len(dims)).astype(np.float32)
+    arrs = [x, x.copy(), x.copy()]
+    return params, [n] * len(dims), [n] * len(dims), [a.ctypes.data for a in arrs[:2]], \
+        [a.ctypes.data for a in arrs], arrs
+
+
+def test_batch_init_rejects_bad_arguments_on_the_host(lib):
+    """Mixed dimensions, FP64 state, an empty list and negative counts are
+    refused before any device work (this runs without a GPU)."""
+    from paper_1908_01682_gb300 import binding as b
+    params, ng, nd, gp, dp, keep = _batch_args(b, dims=(1, 2))
+    rc, h = b.tfsph_batch_init(params, ng, nd, gp, dp, None, b.TFSPH_MEM_HOST)
+    assert rc == b.TFSPH_E_INVALID_ARG and "same dim" in b.tfsph_batch_last_error(None)
+    params, ng, nd, gp, dp, keep = _batch_args(b, precision=1)
+    rc, h = b.tfsph_batch_init(params, ng, nd, gp, dp, None, b.TFSPH_MEM_HOST)
+    assert rc == b.TFSPH_E_INVALID_ARG and "FP32" in b.tfsph_batch_last_error(None)
+    rc, h = b.tfsph_batch_init([], [], [], gp, dp, None, b.TFSPH_MEM_HOST)
+    assert rc == b.TFSPH_E_INVALID_ARG
+    params, ng, nd, gp, dp, keep = _batch_args(b)
+    rc, h = b.tfsph_batch_init(params, [4, -1], nd, gp, dp, None, b.TFSPH_MEM_HOST)
+    assert rc == b.TFSPH_E_INVALID_ARG and "instance 1" in b.tfsph_batch_last_error(None)
+
+
+def test_batch_info_struct_layout():
+    from paper_1908_01682_gb300 import binding as b
+    I = b.tfsph_batch_info_t
+    assert I.n_gas.offset == 8 and I.n_cells.offset == 24 and I.mode.offset == 32
+    assert I.steps.offset == 48 and I.device_bytes.offset == 64 and C.sizeof(I) == 72

@@ -22,56 +22,15 @@ import pytest
 
 import workloads
 from conftest import gpu_context, gpu_lib, gpu_one_step, normwise, oracle_params
+from parity import KAPPA, TOL, UNIT, check_one_step, oracle_step
 
 pytestmark = pytest.mark.gpu
 
-TOL = {0: 1e-5, 1: 1e-12}
-UNIT = {0: 2.0 ** -24, 1: 2.0 ** -53}
-KAPPA = 128.0
-
-
-def _oracle_step(orc, w, tau=None, g=None, **pover):
-    p = oracle_params(w, **pover)
-    s = orc.make_state(p, w.gx, w.gv, w.dx, w.du, w.tstop, ge=w.ge, frozen=w.frozen)
-    r = orc.step(p, s, w.tau if tau is None else tau, w.g if g is None else g)
-    rho_d, _, _ = orc.density(p, w.dx, p.m_dust)
-    return p, s, r, rho_d
-
-
-def _pos_err(a, ref, w):
-    """Normwise position error with periodic differences taken as minimum images."""
-    d = np.asarray(a) - np.asarray(ref)
-    if d.size == 0:
-        return 0.0
-    for k in range(w.dim):
-        if w.params["periodic"][k]:
-            L = w.params["hi"][k] - w.params["lo"][k]
-            d[k] -= L * np.round(d[k] / L)
-    return float(np.linalg.norm(d)) / max(float(np.linalg.norm(ref)), 1e-300)
-
-
-def _cell_mean(values, keys, ncells, mask=None):
-    """Mean of per-particle values over each cell (0 for empty cells)."""
-    m = np.ones_like(values, dtype=bool) if mask is None else mask
-    s = np.bincount(keys[m], weights=values[m], minlength=ncells)
-    n = np.bincount(keys[m], minlength=ncells)
-    return np.where(n > 0, s / np.maximum(n, 1), 0.0)
-
-
-def _bound_ratio(err, bound):
-    """max over elements of |err| / bound (<= 1 passes)."""
-    err = np.abs(np.asarray(err, np.float64))
-    if err.size == 0:
-        return 0.0
-    return float(np.max(err / np.maximum(bound, 1e-300)))
-
-
 def _compare(orc, w, tol=None, **over):
     prec = int(over.get("precision", w.params["precision"]))
-    tol = TOL[prec] if tol is None else tol
-    ku = KAPPA * UNIT[prec]
     gpu = gpu_one_step(w, **over)
-    p, s, r, rho_d = _oracle_step(orc, w)
+    r = orc.step(oracle_params(w), orc.make_state(oracle_params(w), w.gx, w.gv, w.dx, w.du, w.tstop, ge=w.ge,
+                                                  frozen=w.frozen), w.tau, w.g)
     # --- bit-exact integer results ---
     assert np.array_equal(gpu["perm_g"], r.perm_g), "gas sort order"
     assert np.array_equal(gpu["perm_d"], r.perm_d), "dust sort order"
@@ -82,34 +41,7 @@ def _compare(orc, w, tol=None, **over):
     assert np.array_equal(gpu["nb_count"], r.nb_count[r.perm_g]), "neighbour counts"
     assert np.array_equal(gpu["nb_fprint"], r.nb_fprint[r.perm_g]), "neighbour sets"
     # --- floating point after one step ---
-    tau = w.tau
-    ncells = len(r.cstart_g) - 1
-    moving = np.ones(w.n_gas, bool) if w.frozen is None else w.frozen == 0
-    S = r.acc_scale_g
-    S_cell_g = _cell_mean(S, r.keys_g, ncells, moving)
-    errs = {
-        "rho_g": normwise(gpu["rho_g"], r.rho_g),
-        "rho_d": normwise(gpu["rho_d"], rho_d),
-        "gx": _pos_err(gpu["gx"], s.gx, w),
-        "dx": _pos_err(gpu["dx"], s.dx, w),
-    }
-    if w.params["eos"] == 1:
-        errs["ge"] = normwise(gpu["ge"], s.ge)
-    for k, e in errs.items():
-        assert e <= tol, f"{k}: normwise error {e:.3e} > {tol:.0e} ({errs})"
-    ratios = {
-        "acc_g": _bound_ratio(gpu["acc_g"][:, moving] - r.acc_g[:, moving],
-                              tol * np.abs(r.acc_g[:, moving]) + ku * S[moving]),
-        "gv": _bound_ratio(gpu["gv"][:, moving] - s.gv[:, moving],
-                           tol * (np.abs(s.gv[:, moving]) + np.abs(w.gv[:, moving]))
-                           + ku * tau * (S[moving] + S_cell_g[r.keys_g][moving])),
-        "du": _bound_ratio(gpu["du"] - s.du,
-                           tol * (np.abs(s.du) + np.abs(w.du)) + ku * tau * S_cell_g[r.keys_d]),
-    }
-    for k, e in ratios.items():
-        assert e <= 1.0, f"{k}: error / bound = {e:.3e} ({ratios}; normwise {errs})"
-    errs["gv_normwise"] = normwise(gpu["gv"], s.gv)
-    errs["du_normwise"] = normwise(gpu["du"], s.du)
+    r, errs = check_one_step(orc, w, gpu, prec, tol=tol)
     return gpu, r, errs
 
 
@@ -170,7 +102,7 @@ def test_no_gas(orc):
     w = workloads.dustywave(n=50, precision=1)
     w.gx, w.gv = w.gx[:, :0], w.gv[:, :0]
     gpu = gpu_one_step(w)
-    p, s, r, _ = _oracle_step(orc, w)
+    p, s, r, _ = oracle_step(orc, w)
     np.testing.assert_allclose(gpu["du"], s.du, rtol=1e-14, atol=1e-300)
     assert np.array_equal(gpu["cstart_d"], r.cstart_d)
 
@@ -237,7 +169,7 @@ def test_tstop_argument_replaces_resident_values(orc):
         c.step(w.tau, w.g, tstop=new_t)
         gv = c.field(b.TFSPH_FIELD_VEL_G)
         ts = c.field(b.TFSPH_FIELD_TSTOP_D)
-    _, s, _, _ = _oracle_step(orc, w2)
+    _, s, _, _ = oracle_step(orc, w2)
     assert np.array_equal(ts, new_t)
     assert normwise(gv, s.gv) < 1e-12
 
@@ -293,7 +225,7 @@ def test_set_state_restarts_the_run(orc):
         assert c.info().steps == 0
         c.step(w.tau, w.g)
         gv = c.field(b.TFSPH_FIELD_VEL_G)
-    _, s, _, _ = _oracle_step(orc, w)
+    _, s, _, _ = oracle_step(orc, w)
     assert normwise(gv, s.gv) < 1e-12
 
 
