@@ -51,6 +51,7 @@ def parse_args(argv=None):
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-clocks", action="store_true")
     ap.add_argument("--no-adjoint", action="store_true")
+    ap.add_argument("--no-batch", action="store_true")
     return ap.parse_args(argv)
 
 
@@ -408,6 +409,10 @@ def run_ours(args, dist: Dist):
     if not args.no_adjoint:
         adj = run_adjoint(b, args)
 
+    batch = None
+    if not args.no_batch:
+        batch = run_batch(b, args)
+
     cpu = None
     if dist.rank == 0 and dist.world == 1 and not args.no_cpu_baseline:
         cpu = cpu_baseline(args.workload, 0)
@@ -424,6 +429,7 @@ def run_ours(args, dist: Dist):
         "roofline": roof,
         "kernel_ms": {k: round(v, 5) for k, v in phase_avg.items()},
         "adjoint": adj,
+        "batched": batch,
         "cpu_baseline": cpu,
     }
     if dist.rank == 0:
@@ -469,6 +475,87 @@ def run_adjoint(b, args):
     return {"workload": desc, "steps": nsteps, "checkpoint_every": every, "forward_ms": fwd * 1e3,
             "backward_ms": bwd * 1e3, "ratio": bwd / fwd,
             "note": "backward = per-segment recompute + state restores + step adjoints"}
+
+
+def run_batch(b, args):
+    """Batched ensemble: 256 independent 1D dusty waves of 1k-64k particles
+    each (log-uniform sizes, t_stop and amplitudes), stepped as one batch in
+    its autotuned launch form (graph replay), against the same instances
+    stepped one single context after another on the same stream. CUDA events
+    on that stream around each timed loop."""
+    import types
+
+    import numpy as np
+    import torch
+
+    import workloads
+
+    stream = torch.cuda.current_stream()
+    ws = workloads.ensemble1d(precision=0)
+    cell_acc = b.TFSPH_CELL_ACC_FP32 if args.cell_acc == "fp32" else b.TFSPH_CELL_ACC_FP64
+    taus = [w.tau for w in ws]
+    ng = sum(w.n_gas for w in ws)
+    nd = sum(w.n_dust for w in ws)
+    n = ng + nd
+    e0 = torch.cuda.Event(enable_timing=True)
+    e1 = torch.cuda.Event(enable_timing=True)
+
+    def timed(fn, steps):
+        torch.cuda.synchronize()
+        e0.record(stream)
+        fn(steps)
+        e1.record(stream)
+        torch.cuda.synchronize()
+        return e0.elapsed_time(e1) / steps
+
+    items = [(b.params_from_dict(w.params, cell_acc=cell_acc), w.gx, w.gv, w.dx, w.du, w.tstop) for w in ws]
+    bsteps, lsteps = 100, 10
+    with b.Batch(items, stream=stream) as bt:
+        bt.step(taus, nsteps=0)
+        pick = bt.autotune(steps=10)
+        bt.step(nsteps=args.warmup)
+        launches0 = bt.info().launches
+        batched_ms = timed(lambda k: bt.step(nsteps=k), bsteps)
+        info = bt.info()
+        bt.sync()
+        ncells = int(info.n_cells)
+    f32 = lambda a: np.ascontiguousarray(a, dtype=np.float32)
+    ctxs = []
+    try:
+        for w in ws:
+            c = b.Context(b.params_from_dict(w.params, cell_acc=cell_acc), f32(w.gx), f32(w.gv), f32(w.dx),
+                          f32(w.du), f32(w.tstop))
+            c.set_stream(stream)
+            ctxs.append(c)
+
+        def looped(k):
+            for _ in range(k):
+                for c, w in zip(ctxs, ws):
+                    c.step(w.tau, w.g)
+
+        looped(args.warmup)
+        looped_ms = timed(looped, lsteps)
+    finally:
+        for c in ctxs:
+            c.close()
+    wsum = types.SimpleNamespace(n_gas=ng, n_dust=nd)
+    step_bytes = sum(algorithmic(ph, wsum, types.SimpleNamespace(n_cells_total=ncells), 0.0)[1]
+                     for ph in ("count", "scan", "scatter", "gather", "drag")) + (24.0 + 32.0) * ng
+    pk, pk_src = peaks()
+    hbm = float(pk.get("hbm_gbs", 6800.0))
+    return {
+        "workload": f"{len(ws)} independent 1D periodic dusty waves, 1k-64k particles each (log-uniform), "
+                    f"t_stop log-uniform 1e-5..1, amplitudes 1e-5..1e-3, h=1.2dx, cell 2h, FP32",
+        "instances": len(ws), "particles": n, "cells": ncells,
+        "form": {"mode": "persistent" if pick["mode"] == b.TFSPH_BATCH_PERSISTENT else "kernels",
+                 "block": pick["block"], "blocks_per_sm": pick["blocks_per_sm"], "graph": bool(info.graph)},
+        "batched_ms_per_step": batched_ms, "looped_ms_per_step": looped_ms,
+        "speedup_vs_looped": looped_ms / batched_ms,
+        "value": n / (batched_ms * 1e-3), "unit": UNIT,
+        "launches_per_step": (info.launches - launches0) / bsteps,
+        "hbm_frac": (step_bytes / (batched_ms * 1e-3) / 1e9) / hbm, "hbm_peak_gbs": hbm,
+        "steps": {"batched": bsteps, "looped": lsteps},
+    }
 
 
 def run_e2e(b, ctx, w, args, dist):
