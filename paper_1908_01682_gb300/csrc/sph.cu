@@ -127,16 +127,35 @@ __device__ __forceinline__ int halo_seam(const Geo<T> &G, int k, int c0, int hc)
     return G.per[k] && (g < 0 || g >= G.n[k]);
 }
 
-template <class T, int DIM, int MODE, bool SEAM>
+// Appends the neighbours the density walk finds to the particle's list
+// (entries beyond cap are counted, not stored).
+struct NbRec {
+    uint16_t *base;   // entry 0 of the particle
+    size_t stride;    // owned_cap
+    int cap;
+    int n;
+    __device__ __forceinline__ void push(int j, bool seam)
+    {
+        if (n < cap) base[(size_t)n * stride] = (uint16_t)((uint32_t)j | (seam ? kNbSeam : 0u));
+        ++n;
+    }
+};
+
+template <class T, int DIM, int MODE, bool SEAM, bool REC>
 __device__ __forceinline__ void walk_smem_range(PairAcc<T, MODE> &A, const Geo<T> &G, const Phys<T> &Ph,
                                                 const V4<T> &pa, const V4<T> *spos, const V4<T> *svel,
-                                                const T *srho, const uint32_t *sid, int j0, int j1)
+                                                const T *srho, const uint32_t *sid, int j0, int j1, NbRec *rec)
 {
     for (int j = j0; j < j1; ++j) {
         const V4<T> pb = spos[j];
         T d[3];
         const T r2 = pair_r2<T, DIM, SEAM>(G, pa, pb, d);
-        if (ModeUses<MODE>::vel || ModeUses<MODE>::rho) {
+        if (REC) {
+            if (r2 < G.h2x4) {
+                A.add(G, Ph, pb, nullptr, T(1), 0u, r2, d);
+                rec->push(j, SEAM);
+            }
+        } else if (ModeUses<MODE>::vel || ModeUses<MODE>::rho) {
             if (r2 < G.h2x4)
                 A.add(G, Ph, pb, ModeUses<MODE>::vel ? &svel[j] : nullptr, ModeUses<MODE>::rho ? srho[j] : T(1), 0u,
                       r2, d);
@@ -146,11 +165,12 @@ __device__ __forceinline__ void walk_smem_range(PairAcc<T, MODE> &A, const Geo<T
     }
 }
 
-// Candidate walk of one owned particle over the staged tile.
-template <class T, int DIM, int MODE>
+// Candidate walk of one owned particle over the staged tile (REC: the
+// density pass recording the neighbour list).
+template <class T, int DIM, int MODE, bool REC>
 __device__ __forceinline__ void walk_tile(PairAcc<T, MODE> &A, const Geo<T> &G, const Phys<T> &Ph, const TileCfg &C,
                                           const int c0[3], const V4<T> &pa, const int *lstart, const V4<T> *spos,
-                                          const V4<T> *svel, const T *srho, const uint32_t *sid)
+                                          const V4<T> *svel, const T *srho, const uint32_t *sid, NbRec *rec)
 {
     T tx_, ty_ = T(0), tz_ = T(0);
     const int cx = axis_cell(pa.x, G.lo[0], G.inv_w[0], G.n[0], tx_);
@@ -199,8 +219,8 @@ __device__ __forceinline__ void walk_tile(PairAcc<T, MODE> &A, const Geo<T> &G, 
             const int a1 = max(min(u1, sx1), a0);
             const bool inner_seam = (seam_y | seam_z) != 0;
             if (!inner_seam && a1 > a0)
-                walk_smem_range<T, DIM, MODE, false>(A, G, Ph, pa, spos, svel, srho, sid, lstart[hrow + a0],
-                                                     lstart[hrow + a1]);
+                walk_smem_range<T, DIM, MODE, false, REC>(A, G, Ph, pa, spos, svel, srho, sid, lstart[hrow + a0],
+                                                          lstart[hrow + a1], rec);
             if (inner_seam || a0 > u0 || u1 > a1) {
                 // the rare ranges across a seam, visited with the two-sum displacement
                 const int j0 = lstart[hrow + (inner_seam ? u0 : (a0 > u0 ? u0 : a1))];
@@ -211,7 +231,7 @@ __device__ __forceinline__ void walk_tile(PairAcc<T, MODE> &A, const Geo<T> &G, 
                 for (int j = j0; j < j1; ++j) {
                     if (j == jm0) j = jm1;
                     if (j >= j1) break;
-                    walk_smem_range<T, DIM, MODE, true>(A, G, Ph, pa, spos, svel, srho, sid, j, j + 1);
+                    walk_smem_range<T, DIM, MODE, true, REC>(A, G, Ph, pa, spos, svel, srho, sid, j, j + 1, rec);
                 }
             }
         }
@@ -223,7 +243,7 @@ __global__ void __launch_bounds__(kTileThreads, sizeof(T) == 4 ? 3 : 1)
 k_pair_tile(Geo<T> G, Phys<T> Ph, TileCfg C, const V4<T> *__restrict__ pos, const V4<T> *__restrict__ vel,
             const T *__restrict__ rho, const uint32_t *__restrict__ id, const uint32_t *__restrict__ start, T mass,
             T *__restrict__ out_rho, T *pr_out, V4<T> *__restrict__ out_acc, int32_t *__restrict__ cnt,
-            uint64_t *__restrict__ fpr)
+            uint64_t *__restrict__ fpr, NbList nbl)
 {
     extern __shared__ __align__(64) unsigned char smem[];
     __shared__ int wsum[kTileThreads / 32];
@@ -324,7 +344,32 @@ k_pair_tile(Geo<T> G, Phys<T> Ph, TileCfg C, const V4<T> *__restrict__ pos, cons
             const int hrow = C.H[0] * ((oy + (DIM > 1 ? G.R[1] : 0)) + C.H[1] * (oz + (DIM > 2 ? G.R[2] : 0)));
             const V4<T> pa = spos[lstart[hrow + G.R[0]] + k];
             acc_init(A, Ph, pa, vel, rho, a);
-            walk_tile<T, DIM, MODE>(A, G, Ph, C, c0, pa, lstart, spos, svel, srho, sid);
+            const bool listed = nbl.idx && p < nbl.owned_cap;
+            const size_t oc = (size_t)nbl.owned_cap;
+            const size_t lbase = (size_t)blockIdx.x * (size_t)nbl.cap * oc + (size_t)p;
+            if (MODE == 0 && listed) {
+                // density pass: record the neighbours in walk order
+                NbRec rec{nbl.idx + lbase, oc, nbl.cap, 0};
+                walk_tile<T, DIM, MODE, true>(A, G, Ph, C, c0, pa, lstart, spos, svel, srho, sid, &rec);
+                nbl.cnt[(size_t)blockIdx.x * oc + p] = rec.n <= nbl.cap ? (uint16_t)rec.n : kNbNone;
+            } else if (MODE == 2 && listed && nbl.cnt[(size_t)blockIdx.x * oc + p] != kNbNone) {
+                // force pass: the density pass's list of this binning, same order
+                const int n = nbl.cnt[(size_t)blockIdx.x * oc + p];
+                const uint16_t *e = nbl.idx + lbase;
+                const size_t st = oc;
+                uint32_t next = n > 0 ? e[0] : 0u;
+                for (int q = 0; q < n; ++q) {
+                    const uint32_t cur = next;
+                    if (q + 1 < n) next = e[(size_t)(q + 1) * st];
+                    const V4<T> pb = spos[cur & 0x7FFFu];
+                    T d[3];
+                    const T r2 = (cur & kNbSeam) ? pair_r2<T, DIM, true>(G, pa, pb, d)
+                                                 : pair_r2<T, DIM, false>(G, pa, pb, d);
+                    A.add(G, Ph, pb, nullptr, T(1), 0u, r2, d);
+                }
+            } else {
+                walk_tile<T, DIM, MODE, false>(A, G, Ph, C, c0, pa, lstart, spos, svel, srho, sid, nullptr);
+            }
         }
         acc_store(A, Ph, a, mass, vel, out_rho, pr_out, out_acc, cnt, fpr);
     }
@@ -394,7 +439,8 @@ bool plan_tiles(const Geo<T> &G, int dim, double mean, int bytes_pp, int smem_bu
 template <class T, int DIM, int MODE>
 cudaError_t pair_launch(const LaunchCtx &L, const Geo<T> &G, const Phys<T> &Ph, int n, T mass, const V4<T> *pos,
                         const V4<T> *vel, const T *rho, const uint32_t *id, const uint32_t *start, T *out_rho,
-                        T *pr_out, V4<T> *out_acc, int32_t *cnt, uint64_t *fpr, double mean)
+                        T *pr_out, V4<T> *out_acc, int32_t *cnt, uint64_t *fpr, double mean,
+                        NbList nb = NbList{})
 {
     constexpr int bpp = tile_bytes_per_particle<T, MODE>();
     const int budget = (ModeUses<MODE>::vel || ModeUses<MODE>::rho) ? 72 * 1024 : 52 * 1024;
@@ -409,8 +455,10 @@ cudaError_t pair_launch(const LaunchCtx &L, const Geo<T> &G, const Phys<T> &Ph, 
             attr_set = true;
         }
         const int blocks = C.nt[0] * C.nt[1] * C.nt[2];
+        // tile-local indices must fit the list's 15 index bits
+        if (C.cap > 0x7FFF) nb = NbList{};
         k_pair_tile<T, DIM, MODE><<<blocks, kTileThreads, smem, L.stream>>>(G, Ph, C, pos, vel, rho, id, start, mass,
-                                                                            out_rho, pr_out, out_acc, cnt, fpr);
+                                                                            out_rho, pr_out, out_acc, cnt, fpr, nb);
     } else {
         const int threads = 128;
         k_pair_global<T, DIM, MODE><<<(n + threads - 1) / threads, threads, 0, L.stream>>>(
@@ -421,7 +469,7 @@ cudaError_t pair_launch(const LaunchCtx &L, const Geo<T> &G, const Phys<T> &Ph, 
 
 template <class T, int DIM>
 cudaError_t density_t(const LaunchCtx &L, const void *geo, const void *phys, PhaseBufs &P, void *rho, bool gas,
-                      int32_t *cnt, uint64_t *fprint)
+                      int32_t *cnt, uint64_t *fprint, const NbList *nbl)
 {
     if (P.n == 0) return cudaSuccess;
     const Geo<T> &G = *static_cast<const Geo<T> *>(geo);
@@ -435,11 +483,13 @@ cudaError_t density_t(const LaunchCtx &L, const void *geo, const void *phys, Pha
         return pair_launch<T, DIM, 1>(L, G, Ph, (int)P.n, mass, pos, vel, nullptr, P.id[P.cur], P.start,
                                       static_cast<T *>(rho), pr, nullptr, cnt, fprint, mean);
     return pair_launch<T, DIM, 0>(L, G, Ph, (int)P.n, mass, pos, vel, nullptr, P.id[P.cur], P.start,
-                                  static_cast<T *>(rho), pr, nullptr, nullptr, nullptr, mean);
+                                  static_cast<T *>(rho), pr, nullptr, nullptr, nullptr, mean,
+                                  (gas && nbl) ? *nbl : NbList{});
 }
 
 template <class T, int DIM>
-cudaError_t force_t(const LaunchCtx &L, const void *geo, const void *phys, PhaseBufs &P, const void *rho, void *acc)
+cudaError_t force_t(const LaunchCtx &L, const void *geo, const void *phys, PhaseBufs &P, const void *rho, void *acc,
+                    const NbList *nbl)
 {
     if (P.n == 0) return cudaSuccess;
     const Geo<T> &G = *static_cast<const Geo<T> *>(geo);
@@ -452,7 +502,8 @@ cudaError_t force_t(const LaunchCtx &L, const void *geo, const void *phys, Phase
         return pair_launch<T, DIM, 3>(L, G, Ph, (int)P.n, T(0), pos, vel, static_cast<const T *>(rho), P.id[P.cur],
                                       P.start, nullptr, nullptr, static_cast<V4<T> *>(acc), nullptr, nullptr, mean);
     return pair_launch<T, DIM, 2>(L, G, Ph, (int)P.n, T(0), pos, vel, static_cast<const T *>(rho), P.id[P.cur],
-                                  P.start, nullptr, nullptr, static_cast<V4<T> *>(acc), nullptr, nullptr, mean);
+                                  P.start, nullptr, nullptr, static_cast<V4<T> *>(acc), nullptr, nullptr, mean,
+                                  nbl ? *nbl : NbList{});
 }
 
 // lambda_A (V4, storage order) -> lambda_x (V4 .xyz) and lambda_q (.w).
@@ -522,37 +573,70 @@ cudaError_t launch_density_adjoint(const LaunchCtx &L, const void *geo, const vo
 }
 
 cudaError_t launch_density(const LaunchCtx &L, const void *geo, const void *phys, PhaseBufs &P, void *rho, bool gas,
-                           int32_t *cnt, uint64_t *fprint)
+                           int32_t *cnt, uint64_t *fprint, const NbList *nbl)
 {
     if (L.precision == TFSPH_FP64) {
         switch (L.dim) {
-            case 1: return density_t<double, 1>(L, geo, phys, P, rho, gas, cnt, fprint);
-            case 2: return density_t<double, 2>(L, geo, phys, P, rho, gas, cnt, fprint);
-            default: return density_t<double, 3>(L, geo, phys, P, rho, gas, cnt, fprint);
+            case 1: return density_t<double, 1>(L, geo, phys, P, rho, gas, cnt, fprint, nbl);
+            case 2: return density_t<double, 2>(L, geo, phys, P, rho, gas, cnt, fprint, nbl);
+            default: return density_t<double, 3>(L, geo, phys, P, rho, gas, cnt, fprint, nbl);
         }
     }
     switch (L.dim) {
-        case 1: return density_t<float, 1>(L, geo, phys, P, rho, gas, cnt, fprint);
-        case 2: return density_t<float, 2>(L, geo, phys, P, rho, gas, cnt, fprint);
-        default: return density_t<float, 3>(L, geo, phys, P, rho, gas, cnt, fprint);
+        case 1: return density_t<float, 1>(L, geo, phys, P, rho, gas, cnt, fprint, nbl);
+        case 2: return density_t<float, 2>(L, geo, phys, P, rho, gas, cnt, fprint, nbl);
+        default: return density_t<float, 3>(L, geo, phys, P, rho, gas, cnt, fprint, nbl);
     }
 }
 
 cudaError_t launch_force(const LaunchCtx &L, const void *geo, const void *phys, PhaseBufs &G, const void *rho,
-                         void *acc)
+                         void *acc, const NbList *nbl)
 {
     if (L.precision == TFSPH_FP64) {
         switch (L.dim) {
-            case 1: return force_t<double, 1>(L, geo, phys, G, rho, acc);
-            case 2: return force_t<double, 2>(L, geo, phys, G, rho, acc);
-            default: return force_t<double, 3>(L, geo, phys, G, rho, acc);
+            case 1: return force_t<double, 1>(L, geo, phys, G, rho, acc, nbl);
+            case 2: return force_t<double, 2>(L, geo, phys, G, rho, acc, nbl);
+            default: return force_t<double, 3>(L, geo, phys, G, rho, acc, nbl);
         }
     }
     switch (L.dim) {
-        case 1: return force_t<float, 1>(L, geo, phys, G, rho, acc);
-        case 2: return force_t<float, 2>(L, geo, phys, G, rho, acc);
-        default: return force_t<float, 3>(L, geo, phys, G, rho, acc);
+        case 1: return force_t<float, 1>(L, geo, phys, G, rho, acc, nbl);
+        case 2: return force_t<float, 2>(L, geo, phys, G, rho, acc, nbl);
+        default: return force_t<float, 3>(L, geo, phys, G, rho, acc, nbl);
     }
+}
+
+namespace {
+template <class T>
+bool nblist_layout_t(const Geo<T> &G, int dim, int64_t n, int *cap, int *owned_cap, int64_t *tiles)
+{
+    if (n <= 0) return false;
+    double ball = 4.0 * (double)G.h;  // length, area or volume within 2h
+    if (dim == 2) ball = M_PI * 4.0 * (double)G.h * (double)G.h;
+    if (dim == 3) ball = 4.0 / 3.0 * M_PI * 8.0 * (double)G.h * (double)G.h * (double)G.h;
+    double cellv = 1.0;
+    for (int k = 0; k < dim; ++k) cellv *= (double)G.w[k];
+    const double mean = (double)n / (double)G.ncells;
+    const double want = 1.5 * mean * ball / cellv + 16.0;
+    if (want > 1024.0) return false;
+    // the density pass's tiles (MODE 0 plan)
+    TileCfg C{};
+    size_t smem = 0;
+    if (!plan_tiles(G, dim, mean, tile_bytes_per_particle<T, 0>(), 52 * 1024, C, smem) || C.cap > 0x7FFF) return false;
+    double owned = mean;
+    for (int k = 0; k < dim; ++k) owned *= (double)C.T[k];
+    *cap = (int)(32.0 * std::ceil(want / 32.0));
+    *owned_cap = (int)(32.0 * std::ceil((1.25 * owned + 32.0) / 32.0));
+    *tiles = (int64_t)C.nt[0] * C.nt[1] * C.nt[2];
+    return true;
+}
+}  // namespace
+
+bool nblist_layout(const void *geo, int precision, int dim, int64_t n, int *cap, int *owned_cap, int64_t *tiles)
+{
+    if (precision == TFSPH_FP64)
+        return nblist_layout_t(*static_cast<const Geo<double> *>(geo), dim, n, cap, owned_cap, tiles);
+    return nblist_layout_t(*static_cast<const Geo<float> *>(geo), dim, n, cap, owned_cap, tiles);
 }
 
 }  // namespace tfsph

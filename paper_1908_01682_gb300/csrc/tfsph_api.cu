@@ -48,6 +48,8 @@ struct tfsph_ctx {
     void *adj_host = nullptr;  // device mirror of host adjoint arrays
     alignas(64) unsigned char geo[sizeof(Geo<double>)];
     alignas(64) unsigned char phys[sizeof(Phys<double>)];
+    NbList nbl;                 // gas neighbour list of the density pass (nbl.idx null: none)
+    bool nbl_valid = false;     // nbl belongs to the current binning
     bool prepared = false;      // binning and density of the current state are done
     bool forced = false;        // ... and acc holds its pressure acceleration
     bool counts_dirty = false;  // a binning did not finish: zero the cell counts first
@@ -198,6 +200,7 @@ int load_state(tfsph_ctx *c, const void *const *gas, const void *const *dust, co
     c->has_frozen = any_frozen;
     c->prepared = false;
     c->forced = false;
+    c->nbl_valid = false;
     c->steps = 0;
     return TFSPH_OK;
 }
@@ -253,7 +256,9 @@ int prepare(tfsph_ctx *c, cudaEvent_t *ev = nullptr)
     TF_CUDA(c, launch_bin(L, c->geo, c->G, c->D, c->bsum, c->nblk));
     c->counts_dirty = false;
     c->launches += (c->G.n + c->D.n > 0) ? 6 : 3;
-    TF_CUDA(c, launch_density(L, c->geo, c->phys, c->G, c->rho_g, true, nullptr, nullptr));
+    TF_CUDA(c, launch_density(L, c->geo, c->phys, c->G, c->rho_g, true, nullptr, nullptr,
+                              c->nbl.idx ? &c->nbl : nullptr));
+    c->nbl_valid = c->nbl.idx != nullptr;
     if (c->G.n > 0) c->launches += 1;
     if (ev) TF_CUDA(c, cudaEventRecord(ev[TFSPH_PROF_DENSITY + 1], c->stream));
     c->prepared = true;
@@ -268,7 +273,7 @@ int forward_quantities(tfsph_ctx *c, cudaEvent_t *ev = nullptr)
     if (rc) return rc;
     if (c->G.n > 0 && !c->forced) {
         LaunchCtx L = lctx(c);
-        TF_CUDA(c, launch_force(L, c->geo, c->phys, c->G, c->rho_g, c->acc));
+        TF_CUDA(c, launch_force(L, c->geo, c->phys, c->G, c->rho_g, c->acc, c->nbl_valid ? &c->nbl : nullptr));
         c->launches += 1;
     }
     c->forced = true;
@@ -390,6 +395,23 @@ int tfsph_init(tfsph_ctx **out, const tfsph_params *p, const void *const *gas, i
     if ((rc = dalloc(c, &c->rho_g, (size_t)n_gas * c->tsize))) return bail(rc);
     if ((rc = dalloc(c, &c->rho_d, (size_t)n_dust * c->tsize))) return bail(rc);
     if ((rc = dalloc(c, &c->acc, (size_t)n_gas * v4))) return bail(rc);
+    // neighbour list of the gas pair sums (skipped when it would not pay or fit)
+    {
+        int cap = 0, oc = 0;
+        int64_t tiles = 0;
+        if (nblist_layout(c->geo, c->precision, c->dim, n_gas, &cap, &oc, &tiles)) {
+            const size_t bytes = (size_t)tiles * (size_t)cap * (size_t)oc * 2;
+            if (bytes <= ((size_t)16 << 30)) {
+                void *tmp0 = nullptr;
+                if ((rc = dalloc(c, &tmp0, bytes))) return bail(rc);
+                c->nbl.idx = static_cast<uint16_t *>(tmp0);
+                if ((rc = dalloc(c, &tmp0, (size_t)tiles * (size_t)oc * 2))) return bail(rc);
+                c->nbl.cnt = static_cast<uint16_t *>(tmp0);
+                c->nbl.cap = cap;
+                c->nbl.owned_cap = oc;
+            }
+        }
+    }
     c->nblk = ((int64_t)c->ncells + kScanTile - 1) / kScanTile;
     void *tmp;
     if ((rc = dalloc(c, &tmp, (size_t)c->nblk * 2 * 4))) return bail(rc);
@@ -488,6 +510,7 @@ int tfsph_step(tfsph_ctx *c, double tau, const void *t_stop, int mem_kind, const
     }
     c->prepared = false;
     c->forced = false;
+    c->nbl_valid = false;
     c->steps += 1;
     return TFSPH_OK;
 }
@@ -731,6 +754,7 @@ int tfsph_load_state(tfsph_ctx *c, const void *buf, int mem_kind)
     // the per-cell counters are cleared by that binning
     c->prepared = true;
     c->forced = true;
+    c->nbl_valid = false;  // the neighbour list is not part of a snapshot
     c->counts_dirty = true;
     if (h.steps >= 0) c->steps = h.steps;
     return TFSPH_OK;

@@ -96,6 +96,24 @@ struct PhaseBufs {
     int cur = 0;
 };
 
+// Compact neighbour list of the gas pair sums, written by the tiled density
+// pass and read by the tiled force pass of the same binning (both passes use
+// the same tiles and visit the owned particles of a tile in the same order).
+// For owned particle p < owned_cap of tile t, entry k is
+// idx[(t * cap + k) * owned_cap + p]: the tile-local (shared-memory) index of
+// its k-th neighbour in walk order, bit 15 set for a pair across a periodic
+// seam, so a warp's accesses are contiguous. cnt[t * owned_cap + p] is the
+// number of entries, or kNbNone when the particle has more than cap
+// neighbours; such particles (and p >= owned_cap) walk their candidates again.
+struct NbList {
+    uint16_t *idx = nullptr;
+    uint16_t *cnt = nullptr;
+    int cap = 0;
+    int owned_cap = 0;
+};
+constexpr uint16_t kNbNone = 0xFFFFu;
+constexpr uint16_t kNbSeam = 0x8000u;
+
 // Scan partials: blocks of kScanTile cells.
 constexpr int kScanThreads = 256;
 constexpr int kScanItems = 8;
@@ -135,11 +153,17 @@ cudaError_t launch_lam_add_scalar(const LaunchCtx &L, const PhaseBufs &P, const 
 cudaError_t launch_lamq_to_lamrho(const LaunchCtx &L, const PhaseBufs &P, const void *lq, const void *rho, double cs2,
                                   void *lrho);
 
-// sph.cu
+// sph.cu. The density pass writes *nbl when given (gas only), the force pass
+// reads it when given (it must come from the density pass of this binning).
 cudaError_t launch_density(const LaunchCtx &L, const void *geo, const void *phys, PhaseBufs &P,
-                           void *rho, bool gas, int32_t *cnt, uint64_t *fprint);
+                           void *rho, bool gas, int32_t *cnt, uint64_t *fprint, const NbList *nbl = nullptr);
 cudaError_t launch_force(const LaunchCtx &L, const void *geo, const void *phys, PhaseBufs &G,
-                         const void *rho, void *acc);
+                         const void *rho, void *acc, const NbList *nbl = nullptr);
+// Shape of the neighbour list for a gas phase of n particles: entries per
+// particle (about 1.5 times the expected neighbour count, a multiple of 32),
+// owned particles per tile with a list, and tiles; false when the density
+// pass of this geometry is not tiled or its tiles cannot index a list.
+bool nblist_layout(const void *geo, int precision, int dim, int64_t n, int *cap, int *owned_cap, int64_t *tiles);
 cudaError_t launch_force_adjoint(const LaunchCtx &L, const void *geo, const void *phys, PhaseBufs &G,
                                  const void *lamA, void *out);
 cudaError_t launch_density_adjoint(const LaunchCtx &L, const void *geo, const void *phys, PhaseBufs &G,
