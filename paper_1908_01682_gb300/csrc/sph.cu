@@ -357,16 +357,24 @@ k_pair_tile(Geo<T> G, Phys<T> Ph, TileCfg C, const V4<T> *__restrict__ pos, cons
                 const int n = nbl.cnt[(size_t)blockIdx.x * oc + p];
                 const uint16_t *e = nbl.idx + lbase;
                 const size_t st = oc;
-                uint32_t next = n > 0 ? e[0] : 0u;
-                for (int q = 0; q < n; ++q) {
-                    const uint32_t cur = next;
-                    if (q + 1 < n) next = e[(size_t)(q + 1) * st];
+                auto pair = [&](uint32_t cur) {
                     const V4<T> pb = spos[cur & 0x7FFFu];
                     T d[3];
                     const T r2 = (cur & kNbSeam) ? pair_r2<T, DIM, true>(G, pa, pb, d)
                                                  : pair_r2<T, DIM, false>(G, pa, pb, d);
                     A.add(G, Ph, pb, nullptr, T(1), 0u, r2, d);
+                };
+                // entries in groups of 8 independent loads, so one memory
+                // latency covers eight pairs
+                int q = 0;
+                for (; q + 8 <= n; q += 8) {
+                    uint32_t ent[8];
+#pragma unroll
+                    for (int u = 0; u < 8; ++u) ent[u] = e[(size_t)(q + u) * st];
+#pragma unroll
+                    for (int u = 0; u < 8; ++u) pair(ent[u]);
                 }
+                for (; q < n; ++q) pair(e[(size_t)q * st]);
             } else {
                 walk_tile<T, DIM, MODE, false>(A, G, Ph, C, c0, pa, lstart, spos, svel, srho, sid, nullptr);
             }
