@@ -217,16 +217,18 @@ def peaks():
         return {"hbm_gbs": 6800.0, "sm_max_mhz": 2070.0}, "fallback"
 
 
-PHASE_SOURCE = {"count": "bin.cu", "scan": "bin.cu", "scatter": "bin.cu", "gather": "bin.cu",
-                "density": "sph.cu", "force": "sph.cu", "drag": "drag.cu"}
+_BIN = ("bin.cu", "sort_ops.cuh")
+_PAIR = ("sph.cu", "pair.cuh")
+PHASE_SOURCE = {"count": _BIN, "scan": _BIN, "scatter": _BIN, "gather": _BIN,
+                "density": _PAIR, "force": _PAIR, "drag": ("drag.cu", "drag_ops.cuh")}
 
 
 def kernel_source_hash(phase: str) -> str:
-    """sha256 of the phase's kernel source and the shared internal header."""
+    """sha256 of the phase's kernel sources and the shared internal header."""
     import hashlib
     csrc = os.path.join(ROOT, "paper_1908_01682_gb300", "csrc")
     hsh = hashlib.sha256()
-    for f in (PHASE_SOURCE[phase], "tfsph_internal.cuh"):
+    for f in PHASE_SOURCE[phase] + ("tfsph_internal.cuh",):
         with open(os.path.join(csrc, f), "rb") as fh:
             hsh.update(fh.read())
     return hsh.hexdigest()
