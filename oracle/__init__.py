@@ -59,6 +59,12 @@ class _StepOut(C.Structure):
     ]
 
 
+class _XStepOut(C.Structure):
+    _fields_ = [(n, C.c_void_p) for n in (
+        "rho_g", "rho_d", "acc_g", "acc_scale_g", "drag_g", "drag_d", "scale_g", "scale_d",
+        "isph_acc_d", "isph_acc_scale_d", "isph_rho_dg", "isph_K_g", "isph_rho_gd")]
+
+
 _lib = None
 
 
@@ -78,6 +84,7 @@ def _load():
         _lib.orc_max_dt.restype = d
         _lib.orc_max_dt.argtypes = [vp, i64, vp, vp, vp, d]
         _lib.orc_step.argtypes = [vp, i64, i64, vp, vp, vp, vp, vp, vp, vp, d, vp, vp, vp]
+        _lib.orc_step_x.argtypes = [vp, C.c_int, i64, i64, vp, vp, vp, vp, vp, vp, vp, d, vp, vp]
     return _lib
 
 
@@ -263,9 +270,55 @@ def step(p: Params, s: State, tau: float, g=(0.0, 0.0, 0.0), acc_override=None) 
     return r
 
 
-def run(p: Params, s: State, tau: float, nsteps: int, g=(0.0, 0.0, 0.0)) -> State:
+ISPH, MK = 1, 2
+
+
+@dataclass
+class XStepResult:
+    """Diagnostics of one ISPH or MK step (id order). drag_g / drag_d: MK
+    drag accelerations D_a, D_j (Eqs. 8-9); ISPH interpolated velocities u_a
+    (dust at gas particles) and v_j (gas at dust particles) (Eq. 11)."""
+    rho_g: np.ndarray
+    rho_d: np.ndarray
+    acc_g: np.ndarray
+    acc_scale_g: np.ndarray
+    drag_g: np.ndarray
+    drag_d: np.ndarray
+    scale_g: np.ndarray
+    scale_d: np.ndarray
+    isph_acc_d: np.ndarray
+    isph_acc_scale_d: np.ndarray
+    isph_rho_dg: np.ndarray
+    isph_K_g: np.ndarray
+    isph_rho_gd: np.ndarray
+
+
+def step_x(p: Params, s: State, tau: float, g=(0.0, 0.0, 0.0), scheme: int = ISPH) -> XStepResult:
+    """One step with the ISPH (Eqs. 11-16) or MK (Eqs. 8-10) drag, in place on ``s``."""
+    ng = s.gx.shape[1]
+    nd = s.dx.shape[1]
+    dim = p.dim
+    r = XStepResult(np.zeros(ng), np.zeros(nd), np.zeros((dim, ng)), np.zeros(ng), np.zeros((dim, ng)),
+                    np.zeros((dim, nd)), np.zeros(ng), np.zeros(nd), np.zeros((dim, nd)), np.zeros(nd),
+                    np.zeros(ng), np.zeros(ng), np.zeros(nd))
+    out = _XStepOut(*[_ptr(getattr(r, f[0])) for f in _XStepOut._fields_])
+    g3 = (C.c_double * 3)(*[float(g[k]) if k < len(g) else 0.0 for k in range(3)])
+    pc = p.c()
+    rc = _load().orc_step_x(C.byref(pc), int(scheme), ng, nd, _ptr(s.gx), _ptr(s.gv), _ptr(s.ge),
+                            _ptr(s.frozen), _ptr(s.dx), _ptr(s.du), _ptr(s.tstop), float(tau), g3,
+                            C.byref(out))
+    if rc != 0:
+        raise RuntimeError(f"orc_step_x failed with code {rc}")
+    return r
+
+
+def run(p: Params, s: State, tau: float, nsteps: int, g=(0.0, 0.0, 0.0), scheme: int = 0) -> State:
+    """nsteps steps; scheme 0 = IDIC, ISPH or MK."""
     for _ in range(nsteps):
-        step(p, s, tau, g)
+        if scheme == 0:
+            step(p, s, tau, g)
+        else:
+            step_x(p, s, tau, g, scheme)
     return s
 
 

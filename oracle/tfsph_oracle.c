@@ -741,3 +741,389 @@ done:
     free(cN); free(cL); free(cv); free(cu); free(cA); free(ct);
     return rc;
 }
+
+/* ======================================================================== */
+/* The two other drag schemes the paper compares (Sec. 2.1, 2.2), on the    */
+/* same gas pressure force and binning.                                     */
+/*                                                                          */
+/* Drag coefficient: the path takes the stopping time t_j of every dust     */
+/* particle as input, so K = rho_d / t_stop (the definition of Eq. 7) is    */
+/* used throughout, with rho_d the dust summation density:                  */
+/*   MK:   K_aj = rho_j,d / t_j, so K_aj / (rho_a,g rho_j,d) = 1/(rho_a,g t_j) */
+/*   ISPH: at a dust particle K_j = rho_j,d / t_j; at a gas particle K is   */
+/*         SPH-interpolated like any dust field (Eq. 11 form):              */
+/*         K_a = m_d sum_j (K_j / rho_j,d) W_aj = m_d sum_j W_aj / t_j.     */
+/* Frozen (wall) gas particles enter the density and pressure sums and take */
+/* no part in the drag (they are at rest and never move).                   */
+/* ======================================================================== */
+
+/* Cross-phase candidate walk: the neighbours, among the particles of the   */
+/* grid G (the other phase), of a point p; membership as for gas pairs.     */
+typedef struct {
+    const orc_grid *G;
+    double p[3];
+    void (*pair)(void *ctx, int64_t b, const double d[3], double r2);
+    void *ctx;
+} orc_cross_ctx;
+
+static void orc_cross_visit(void *vctx, int64_t b)
+{
+    orc_cross_ctx *c = (orc_cross_ctx *)vctx;
+    double pb[3], d[3], r2;
+    orc_get_pos(c->G->P->dim, c->G->n, c->G->x, b, pb);
+    if (!orc_pair(c->G->P, c->p, pb, d, &r2)) return;
+    c->pair(c->ctx, b, d, r2);  /* d = p - x_b */
+}
+
+static void orc_cross_walk(const orc_grid *G, const double p[3],
+                           void (*pair)(void *, int64_t, const double *, double), void *ctx)
+{
+    orc_cross_ctx c;
+    c.G = G;
+    for (int k = 0; k < 3; ++k) c.p[k] = p[k];
+    c.pair = pair;
+    c.ctx = ctx;
+    orc_foreach_candidate(G, p, orc_cross_visit, &c);
+}
+
+/* --- MK (Eqs. 8-10), explicit in the drag:                               */
+/*   D_a = - sigma m_d sum_j K_aj/(rho_a,g rho_j,d) ((v_a - u_j).r_ja)       */
+/*                          / (r_ja^2 + eta^2) r_ja W_ja                     */
+/*   D_j = + sigma m_g sum_a (same pair factor)                              */
+/* r_ja = r_j - r_a (the product ((v_a - u_j).r) r is even in r), eta^2 =    */
+/* 0.001 h^2, sigma = the dimension (1 in 1D, as the paper states).          */
+typedef struct {
+    const orc_params *P;
+    int64_t nsrc;
+    const double *vsrc;       /* other phase velocities (dim x nsrc) */
+    const double *coef_src;   /* per source: 1/t_j (gas target) or 1/rho_a,g (dust target) */
+    const uint8_t *skip_src;  /* frozen gas sources (dust target), nullable */
+    double vt[3];             /* target velocity */
+    double coef_t;            /* per target: 1/rho_a,g (gas target) or 1/t_j (dust target) */
+    double sign;              /* v_gas - u_dust = sign * (v_target - v_source) */
+    double sum[3];
+    double scale;
+} orc_mk_ctx;
+
+static void orc_mk_pair(void *vctx, int64_t b, const double d[3], double r2)
+{
+    orc_mk_ctx *c = (orc_mk_ctx *)vctx;
+    const orc_params *P = c->P;
+    if (c->skip_src && c->skip_src[b]) return;
+    double rel = 0.0;
+    for (int k = 0; k < P->dim; ++k)
+        rel += c->sign * (c->vt[k] - c->vsrc[(int64_t)k * c->nsrc + b]) * d[k];
+    double w = orc_W(P->dim, P->h, sqrt(r2));
+    double f = c->coef_t * c->coef_src[b] * rel / (r2 + 0.001 * P->h * P->h) * w;
+    double dn = 0.0;
+    for (int k = 0; k < P->dim; ++k) {
+        c->sum[k] += f * d[k];
+        dn += d[k] * d[k];
+    }
+    c->scale += fabs(f) * sqrt(dn);
+}
+
+/* --- ISPH interpolation at a gas particle a over dust j (Eq. 11 form):   */
+/*   rho^d_a = m_d sum_j W_aj,  K_a = m_d sum_j W_aj / t_j,                 */
+/*   u_a = m_d sum_j u_j / rho_j,d W_aj.                                    */
+typedef struct {
+    const orc_params *P;
+    int64_t nd;
+    const double *du, *tstop, *rho_d;
+    double rho, K, u[3];
+    double uscale;   /* m_d sum_j |u_j| / rho_j,d W_aj */
+} orc_isph_g_ctx;
+
+static void orc_isph_g_pair(void *vctx, int64_t j, const double d[3], double r2)
+{
+    orc_isph_g_ctx *c = (orc_isph_g_ctx *)vctx;
+    const orc_params *P = c->P;
+    (void)d;
+    double w = P->m_dust * orc_W(P->dim, P->h, sqrt(r2));
+    c->rho += w;
+    c->K += w / c->tstop[j];
+    double un = 0.0;
+    for (int k = 0; k < P->dim; ++k) {
+        double uk = c->du[(int64_t)k * c->nd + j];
+        c->u[k] += w * uk / c->rho_d[j];
+        un += uk * uk;
+    }
+    c->uscale += w * sqrt(un) / c->rho_d[j];
+}
+
+/* --- ISPH interpolation at a dust particle j over gas a (Eqs. 11, 14):   */
+/*   rho^g_j = m_g sum_a W_aj,  v_j = m_g sum_{a moving} v_a / rho_a W_aj,  */
+/*   e_j = m_g sum_a e_a / rho_a W_aj (adiabatic gas),                      */
+/*   G_j = m_g sum_a grad_j W_aj,  Q_j = m_g sum_a q_a grad_j W_aj,         */
+/* q_a = p_a / rho_a^2; then the pressure acceleration at j (Eq. 14) is     */
+/*   A_j = - (Q_j + q_j G_j),  q_j = p_j / (rho^g_j)^2.                     */
+typedef struct {
+    const orc_params *P;
+    int64_t ng;
+    const double *gv, *ge, *rho_g, *q;
+    const uint8_t *frozen;
+    double rho, e, v[3], Gs[3], Qs[3];
+    double vscale, gscale, qscale;
+} orc_isph_d_ctx;
+
+static void orc_isph_d_pair(void *vctx, int64_t a, const double d[3], double r2)
+{
+    orc_isph_d_ctx *c = (orc_isph_d_ctx *)vctx;
+    const orc_params *P = c->P;
+    double r = sqrt(r2);
+    double w = P->m_gas * orc_W(P->dim, P->h, r);
+    c->rho += w;
+    if (P->eos == 1 && c->ge) c->e += w * c->ge[a] / c->rho_g[a];
+    if (!(c->frozen && c->frozen[a])) {
+        double vn = 0.0;
+        for (int k = 0; k < P->dim; ++k) {
+            double vk = c->gv[(int64_t)k * c->ng + a];
+            c->v[k] += w * vk / c->rho_g[a];
+            vn += vk * vk;
+        }
+        c->vscale += w * sqrt(vn) / c->rho_g[a];
+    }
+    if (r > 0.0) {
+        /* d = x_j - x_a: grad_j W_aj = d / r dW/dr */
+        double dw = P->m_gas * orc_dWdr(P->dim, P->h, r) / r;
+        double gn = 0.0;
+        for (int k = 0; k < P->dim; ++k) {
+            c->Gs[k] += dw * d[k];
+            c->Qs[k] += c->q[a] * dw * d[k];
+            gn += d[k] * d[k];
+        }
+        c->gscale += fabs(dw) * sqrt(gn);
+        c->qscale += fabs(c->q[a] * dw) * sqrt(gn);
+    }
+}
+
+typedef struct {
+    /* outputs, each nullable (id order) */
+    double *rho_g;       /* [ng] gas density */
+    double *rho_d;       /* [nd] dust density */
+    double *acc_g;       /* [dim*ng] gas pressure (+viscous) acceleration */
+    double *acc_scale_g; /* [ng] */
+    double *drag_g;      /* [dim*ng] MK: D_a; ISPH: interpolated dust velocity u_a */
+    double *drag_d;      /* [dim*nd] MK: D_j; ISPH: interpolated gas velocity v_j */
+    double *scale_g;     /* [ng] MK: magnitude sum of D_a's terms; ISPH: of u_a's */
+    double *scale_d;     /* [nd] MK: of D_j's terms; ISPH: of v_j's */
+    double *isph_acc_d;  /* [dim*nd] ISPH: pressure acceleration at the dust particle (Eq. 14) */
+    double *isph_acc_scale_d; /* [nd] ISPH: its condition scale */
+    double *isph_rho_dg; /* [ng] ISPH: interpolated dust density at gas particles */
+    double *isph_K_g;    /* [ng] ISPH: interpolated K at gas particles */
+    double *isph_rho_gd; /* [nd] ISPH: interpolated gas density at dust particles */
+} orc_xstep_out;
+
+/* One step with drag scheme 1 (ISPH, Eqs. 11-16) or 2 (MK, Eqs. 8-10), in  */
+/* place; binning, densities, gas pressure force and the position update as */
+/* in orc_step.                                                              */
+/*   ISPH, each particle with neighbours of the other phase: the 2x2 system  */
+/*     (v' - v)/tau = A + g - alpha (v' - u'),  (u' - u)/tau = g + beta (v' - u') */
+/*   in (own velocity, interpolated velocity of the other phase), alpha =    */
+/*   K / rho_g, beta = K / rho_d at the particle (Eqs. 12-16), solved by      */
+/*     w' = (v - u + tau A) / (1 + tau (alpha + beta)),                      */
+/*     v' = v + tau (A + g) - tau alpha w',   u' = u + tau g + tau beta w';   */
+/*   a gas particle keeps v', a dust particle keeps u'. The paper's Eq. 15    */
+/*   divides by rho^n_{a,d} where the dust density at j, rho^n_{j,d}, is      */
+/*   meant (Eq. 15 is the equation of dust particle j).                       */
+/*   MK: v_a' = v_a + tau (A_a + D_a + g), u_j' = u_j + tau (D_j + g).        */
+int orc_step_x(const orc_params *P, int scheme, int64_t ng, int64_t nd,
+               double *gx, double *gv, double *ge, const uint8_t *gfrozen,
+               double *dx, double *du, const double *tstop,
+               double tau, const double g[3], orc_xstep_out *out)
+{
+    int dim = P->dim;
+    if (dim < 1 || dim > 3 || tau <= 0.0 || (scheme != 1 && scheme != 2)) return ORC_E_ARG;
+    size_t sg = (size_t)(ng > 0 ? ng : 1), sd = (size_t)(nd > 0 ? nd : 1);
+    double *rho_g = (double *)calloc(sg, sizeof(double));
+    double *rho_d = (double *)calloc(sd, sizeof(double));
+    double *acc = (double *)calloc((size_t)dim * sg, sizeof(double));
+    double *dedt = (double *)calloc(sg, sizeof(double));
+    double *ascale = (double *)calloc(sg, sizeof(double));
+    double *q = (double *)calloc(sg, sizeof(double));
+    double *Xg = (double *)calloc((size_t)dim * sg, sizeof(double));  /* D_a or u_a */
+    double *Xd = (double *)calloc((size_t)dim * sd, sizeof(double));  /* D_j or v_j */
+    double *Sg = (double *)calloc(sg, sizeof(double));
+    double *Sd = (double *)calloc(sd, sizeof(double));
+    double *Ad = (double *)calloc((size_t)dim * sd, sizeof(double));  /* ISPH A_j */
+    double *ASd = (double *)calloc(sd, sizeof(double));
+    double *rdg = (double *)calloc(sg, sizeof(double));               /* ISPH rho^d_a */
+    double *Kg = (double *)calloc(sg, sizeof(double));                /* ISPH K_a */
+    double *rgd = (double *)calloc(sd, sizeof(double));               /* ISPH rho^g_j */
+    double *inv_t = (double *)calloc(sd, sizeof(double));
+    double *inv_rho = (double *)calloc(sg, sizeof(double));
+    orc_grid Gg, Gd;
+    int64_t *pg = NULL, *cg = NULL, *pd = NULL, *cd = NULL;
+    int rc = ORC_OK;
+    if (!rho_g || !rho_d || !acc || !dedt || !ascale || !q || !Xg || !Xd || !Sg || !Sd || !Ad || !ASd ||
+        !rdg || !Kg || !rgd || !inv_t || !inv_rho || orc_make_grid(P, ng, gx, &Gg, &pg, &cg) != ORC_OK ||
+        orc_make_grid(P, nd, dx, &Gd, &pd, &cd) != ORC_OK) {
+        rc = ORC_E_OOM;
+        goto done;
+    }
+    /* densities, pressure and the gas pressure force */
+    if (ng > 0) orc_density(P, ng, gx, P->m_gas, rho_g, NULL, NULL);
+    if (nd > 0) orc_density(P, nd, dx, P->m_dust, rho_d, NULL, NULL);
+    if (ng > 0) orc_accel(P, ng, gx, gv, ge, rho_g, acc, dedt, ascale);
+    for (int64_t a = 0; a < ng; ++a) {
+        q[a] = orc_pressure(P, rho_g[a], ge ? ge[a] : 0.0) / (rho_g[a] * rho_g[a]);
+        inv_rho[a] = 1.0 / rho_g[a];
+    }
+    for (int64_t j = 0; j < nd; ++j) inv_t[j] = 1.0 / tstop[j];
+
+    /* cross-phase sums at every gas particle (over dust) and every dust     */
+    /* particle (over gas)                                                   */
+#pragma omp parallel for schedule(dynamic, 256)
+    for (int64_t a = 0; a < ng; ++a) {
+        if (gfrozen && gfrozen[a]) continue;
+        double pa[3];
+        orc_get_pos(dim, ng, gx, a, pa);
+        if (scheme == 2) {
+            orc_mk_ctx c;
+            memset(&c, 0, sizeof c);
+            c.P = P;
+            c.nsrc = nd;
+            c.vsrc = du;
+            c.coef_src = inv_t;
+            c.skip_src = NULL;
+            for (int k = 0; k < dim; ++k) c.vt[k] = gv[(int64_t)k * ng + a];
+            c.coef_t = inv_rho[a];
+            c.sign = 1.0;
+            orc_cross_walk(&Gd, pa, orc_mk_pair, &c);
+            for (int k = 0; k < dim; ++k) Xg[(int64_t)k * ng + a] = -(double)dim * P->m_dust * c.sum[k];
+            Sg[a] = (double)dim * P->m_dust * c.scale;
+        } else {
+            orc_isph_g_ctx c;
+            memset(&c, 0, sizeof c);
+            c.P = P;
+            c.nd = nd;
+            c.du = du;
+            c.tstop = tstop;
+            c.rho_d = rho_d;
+            orc_cross_walk(&Gd, pa, orc_isph_g_pair, &c);
+            for (int k = 0; k < dim; ++k) Xg[(int64_t)k * ng + a] = c.u[k];
+            Sg[a] = c.uscale;
+            rdg[a] = c.rho;
+            Kg[a] = c.K;
+        }
+    }
+#pragma omp parallel for schedule(dynamic, 256)
+    for (int64_t j = 0; j < nd; ++j) {
+        double pj[3];
+        orc_get_pos(dim, nd, dx, j, pj);
+        if (scheme == 2) {
+            orc_mk_ctx c;
+            memset(&c, 0, sizeof c);
+            c.P = P;
+            c.nsrc = ng;
+            c.vsrc = gv;
+            c.coef_src = inv_rho;
+            c.skip_src = gfrozen;
+            for (int k = 0; k < dim; ++k) c.vt[k] = du[(int64_t)k * nd + j];
+            c.coef_t = inv_t[j];
+            c.sign = -1.0;
+            orc_cross_walk(&Gg, pj, orc_mk_pair, &c);
+            for (int k = 0; k < dim; ++k) Xd[(int64_t)k * nd + j] = (double)dim * P->m_gas * c.sum[k];
+            Sd[j] = (double)dim * P->m_gas * c.scale;
+        } else {
+            orc_isph_d_ctx c;
+            memset(&c, 0, sizeof c);
+            c.P = P;
+            c.ng = ng;
+            c.gv = gv;
+            c.ge = ge;
+            c.rho_g = rho_g;
+            c.q = q;
+            c.frozen = gfrozen;
+            orc_cross_walk(&Gg, pj, orc_isph_d_pair, &c);
+            rgd[j] = c.rho;
+            double qj = 0.0;
+            if (c.rho > 0.0) {
+                /* p_j / rho_j^2: isothermal cs^2 / rho; adiabatic (gamma-1) e_j / rho */
+                qj = P->eos == 1 ? (P->gamma - 1.0) * c.e / c.rho : P->cs * P->cs / c.rho;
+            }
+            double an = 0.0;
+            for (int k = 0; k < dim; ++k) {
+                Xd[(int64_t)k * nd + j] = c.v[k];
+                Ad[(int64_t)k * nd + j] = -(c.Qs[k] + qj * c.Gs[k]);
+            }
+            (void)an;
+            Sd[j] = c.vscale;
+            ASd[j] = c.qscale + fabs(qj) * c.gscale;
+        }
+    }
+
+    /* velocity updates */
+    for (int64_t a = 0; a < ng; ++a) {
+        if (gfrozen && gfrozen[a]) continue;
+        for (int k = 0; k < dim; ++k) {
+            double v = gv[(int64_t)k * ng + a], A = acc[(int64_t)k * ng + a];
+            double vn;
+            if (scheme == 2) {
+                vn = v + tau * (A + Xg[(int64_t)k * ng + a] + g[k]);
+            } else if (rdg[a] > 0.0) {
+                double alpha = Kg[a] / rho_g[a], beta = Kg[a] / rdg[a];
+                double wn = (v - Xg[(int64_t)k * ng + a] + tau * A) / (1.0 + tau * (alpha + beta));
+                vn = v + tau * (A + g[k]) - tau * alpha * wn;
+            } else {
+                vn = v + tau * (A + g[k]);
+            }
+            gv[(int64_t)k * ng + a] = vn;
+        }
+        if (P->eos == 1 && ge) ge[a] += tau * dedt[a];
+    }
+    for (int64_t j = 0; j < nd; ++j) {
+        for (int k = 0; k < dim; ++k) {
+            double u = du[(int64_t)k * nd + j];
+            double un;
+            if (scheme == 2) {
+                un = u + tau * (Xd[(int64_t)k * nd + j] + g[k]);
+            } else if (rgd[j] > 0.0) {
+                double alpha = rho_d[j] / (rgd[j] * tstop[j]), beta = 1.0 / tstop[j];
+                double wn = (Xd[(int64_t)k * nd + j] - u + tau * Ad[(int64_t)k * nd + j]) /
+                            (1.0 + tau * (alpha + beta));
+                un = u + tau * g[k] + tau * beta * wn;
+            } else {
+                un = u + tau * g[k];
+            }
+            du[(int64_t)k * nd + j] = un;
+        }
+    }
+    /* positions */
+    for (int64_t a = 0; a < ng; ++a) {
+        if (gfrozen && gfrozen[a]) continue;
+        for (int k = 0; k < dim; ++k) {
+            double xn = gx[(int64_t)k * ng + a] + tau * gv[(int64_t)k * ng + a];
+            if (P->periodic[k]) xn = orc_wrap(xn, P->lo[k], P->hi[k]);
+            gx[(int64_t)k * ng + a] = xn;
+        }
+    }
+    for (int64_t j = 0; j < nd; ++j) {
+        for (int k = 0; k < dim; ++k) {
+            double xn = dx[(int64_t)k * nd + j] + tau * du[(int64_t)k * nd + j];
+            if (P->periodic[k]) xn = orc_wrap(xn, P->lo[k], P->hi[k]);
+            dx[(int64_t)k * nd + j] = xn;
+        }
+    }
+    if (out) {
+        size_t bg = sizeof(double) * (size_t)ng, bd = sizeof(double) * (size_t)nd;
+        if (out->rho_g) memcpy(out->rho_g, rho_g, bg);
+        if (out->rho_d) memcpy(out->rho_d, rho_d, bd);
+        if (out->acc_g) memcpy(out->acc_g, acc, bg * dim);
+        if (out->acc_scale_g) memcpy(out->acc_scale_g, ascale, bg);
+        if (out->drag_g) memcpy(out->drag_g, Xg, bg * dim);
+        if (out->drag_d) memcpy(out->drag_d, Xd, bd * dim);
+        if (out->scale_g) memcpy(out->scale_g, Sg, bg);
+        if (out->scale_d) memcpy(out->scale_d, Sd, bd);
+        if (out->isph_acc_d) memcpy(out->isph_acc_d, Ad, bd * dim);
+        if (out->isph_acc_scale_d) memcpy(out->isph_acc_scale_d, ASd, bd);
+        if (out->isph_rho_dg) memcpy(out->isph_rho_dg, rdg, bg);
+        if (out->isph_K_g) memcpy(out->isph_K_g, Kg, bg);
+        if (out->isph_rho_gd) memcpy(out->isph_rho_gd, rgd, bd);
+    }
+done:
+    free(rho_g); free(rho_d); free(acc); free(dedt); free(ascale); free(q); free(Xg); free(Xd);
+    free(Sg); free(Sd); free(Ad); free(ASd); free(rdg); free(Kg); free(rgd); free(inv_t); free(inv_rho);
+    free(pg); free(cg); free(pd); free(cd);
+    return rc;
+}
