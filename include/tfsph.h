@@ -69,6 +69,14 @@ extern "C" {
 #define TFSPH_CELL_ACC_FP32 0   /* per-cell sums and drag solve in float */
 #define TFSPH_CELL_ACC_FP64 1   /* per-cell sums and drag solve in double */
 
+/* drag scheme (tfsph_params.drag). K = rho_d / t_stop (Eq. 7) with the
+ * per-particle stopping times throughout. */
+#define TFSPH_DRAG_IDIC 0  /* implicit drag in cell (Sec. 2.3, Eqs. 17-21) */
+#define TFSPH_DRAG_ISPH 1  /* semi-implicit SPH interpolation (Sec. 2.2, Eqs. 11-16): per particle,
+                              the other phase's velocity, density and K interpolated at it */
+#define TFSPH_DRAG_MK   2  /* explicit pairwise drag (Sec. 2.1, Eqs. 8-10); stable only for
+                              tau below t_stop (Eq. 5) */
+
 /* fields for tfsph_fields; vector fields are written component-major, out[k*n + i] */
 #define TFSPH_FIELD_POS_G    0  /* dim x n_gas */
 #define TFSPH_FIELD_VEL_G    1  /* dim x n_gas */
@@ -106,7 +114,7 @@ typedef struct {
     int32_t periodic[3];  /* 1 = periodic axis, 0 = open axis (walls are frozen gas particles) */
     int32_t tstar_mode;   /* TFSPH_TSTAR_* */
     int32_t cell_acc;     /* TFSPH_CELL_ACC_*; forced to FP64 when precision is FP64 */
-    int32_t reserved;     /* must be 0 */
+    int32_t drag;         /* TFSPH_DRAG_*: IDIC (Sec. 2.3, 0), ISPH (Sec. 2.2) or MK (Sec. 2.1) */
     double lo[3], hi[3];  /* box; periodic axes need hi - lo >= 4h */
     double h;             /* smoothing length (> 0), kernel support 2h */
     double cell_size;     /* requested cell edge (> 0) */

@@ -28,6 +28,7 @@ TFSPH_EOS_ISOTHERMAL, TFSPH_EOS_ADIABATIC = 0, 1
 TFSPH_KERNEL_CUBIC = 0
 TFSPH_TSTAR_ARITHMETIC, TFSPH_TSTAR_HARMONIC = 0, 1
 TFSPH_CELL_ACC_FP32, TFSPH_CELL_ACC_FP64 = 0, 1
+TFSPH_DRAG_IDIC, TFSPH_DRAG_ISPH, TFSPH_DRAG_MK = 0, 1, 2
 (TFSPH_FIELD_POS_G, TFSPH_FIELD_VEL_G, TFSPH_FIELD_ENERGY_G, TFSPH_FIELD_RHO_G, TFSPH_FIELD_POS_D,
  TFSPH_FIELD_VEL_D, TFSPH_FIELD_TSTOP_D, TFSPH_FIELD_RHO_D) = range(8)
 TFSPH_ORDER_ORIGINAL, TFSPH_ORDER_CELL = 0, 1
@@ -41,7 +42,7 @@ class tfsph_params(C.Structure):
     _fields_ = [
         ("dim", C.c_int32), ("precision", C.c_int32), ("kernel", C.c_int32), ("eos", C.c_int32),
         ("periodic", C.c_int32 * 3), ("tstar_mode", C.c_int32), ("cell_acc", C.c_int32),
-        ("reserved", C.c_int32),
+        ("drag", C.c_int32),
         ("lo", C.c_double * 3), ("hi", C.c_double * 3),
         ("h", C.c_double), ("cell_size", C.c_double), ("m_gas", C.c_double), ("m_dust", C.c_double),
         ("cs", C.c_double), ("gamma", C.c_double), ("av_alpha", C.c_double), ("av_beta", C.c_double),
@@ -313,10 +314,10 @@ def tfsph_batch_destroy(b) -> None:
 # ---------------------------------------------------------------------------
 def make_params(dim, lo, hi, periodic, h, cell_size, m_gas, m_dust, precision=TFSPH_FP32,
                 eos=TFSPH_EOS_ISOTHERMAL, cs=1.0, gamma=1.4, av_alpha=0.0, av_beta=0.0,
-                tstar_mode=TFSPH_TSTAR_ARITHMETIC, cell_acc=TFSPH_CELL_ACC_FP64) -> tfsph_params:
+                tstar_mode=TFSPH_TSTAR_ARITHMETIC, cell_acc=TFSPH_CELL_ACC_FP64, drag=TFSPH_DRAG_IDIC) -> tfsph_params:
     p = tfsph_params()
     p.dim, p.precision, p.kernel, p.eos = int(dim), int(precision), TFSPH_KERNEL_CUBIC, int(eos)
-    p.tstar_mode, p.cell_acc, p.reserved = int(tstar_mode), int(cell_acc), 0
+    p.tstar_mode, p.cell_acc, p.drag = int(tstar_mode), int(cell_acc), int(drag)
     for k in range(3):
         p.periodic[k] = int(periodic[k]) if k < len(periodic) else 0
         p.lo[k] = float(lo[k]) if k < len(lo) else 0.0
@@ -332,7 +333,8 @@ def params_from_dict(d: dict, **overrides) -> tfsph_params:
     return make_params(q["dim"], q["lo"], q["hi"], q["periodic"], q["h"], q["cell_size"], q["m_gas"],
                        q["m_dust"], precision=q.get("precision", 0), eos=q.get("eos", 0), cs=q.get("cs", 1.0),
                        gamma=q.get("gamma", 1.4), av_alpha=q.get("av_alpha", 0.0), av_beta=q.get("av_beta", 0.0),
-                       tstar_mode=q.get("tstar_mode", 0), cell_acc=q.get("cell_acc", TFSPH_CELL_ACC_FP64))
+                       tstar_mode=q.get("tstar_mode", 0), cell_acc=q.get("cell_acc", TFSPH_CELL_ACC_FP64),
+                       drag=q.get("drag", TFSPH_DRAG_IDIC))
 
 
 def _check(rc: int, ctx=None):

@@ -935,6 +935,8 @@ int tfsph_batch_init(tfsph_batch **out, const tfsph_params *params, const int64_
         if (p.dim != p0.dim || p.precision != TFSPH_FP32 || p.tstar_mode != p0.tstar_mode || p.cell_acc != p0.cell_acc)
             return bfail(nullptr, TFSPH_E_INVALID_ARG,
                          "every instance of a batch needs the same dim, tstar_mode and cell_acc, and FP32 precision");
+        if (p.drag != TFSPH_DRAG_IDIC)
+            return bfail(nullptr, TFSPH_E_INVALID_ARG, "batches run the IDIC drag");
         int nc3[3];
         ncells += cell_grid(p, nc3);
         ng += n_gas[i];

@@ -18,7 +18,7 @@ int validate_params(const tfsph_params *p, int64_t ng, int64_t nd, std::string &
     if (p->eos != TFSPH_EOS_ISOTHERMAL && p->eos != TFSPH_EOS_ADIABATIC) { why = "unknown eos"; return TFSPH_E_INVALID_ARG; }
     if (p->tstar_mode != TFSPH_TSTAR_ARITHMETIC && p->tstar_mode != TFSPH_TSTAR_HARMONIC) { why = "unknown tstar_mode"; return TFSPH_E_INVALID_ARG; }
     if (p->cell_acc != TFSPH_CELL_ACC_FP32 && p->cell_acc != TFSPH_CELL_ACC_FP64) { why = "unknown cell_acc"; return TFSPH_E_INVALID_ARG; }
-    if (p->reserved != 0) { why = "reserved must be 0"; return TFSPH_E_INVALID_ARG; }
+    if (p->drag != TFSPH_DRAG_IDIC && p->drag != TFSPH_DRAG_ISPH && p->drag != TFSPH_DRAG_MK) { why = "unknown drag scheme"; return TFSPH_E_INVALID_ARG; }
     const double vals[] = {p->h, p->cell_size, p->m_gas, p->m_dust, p->cs, p->gamma, p->av_alpha, p->av_beta};
     for (double v : vals)
         if (!std::isfinite(v)) { why = "non-finite parameter"; return TFSPH_E_NONFINITE; }

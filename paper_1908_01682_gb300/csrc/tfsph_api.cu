@@ -49,6 +49,7 @@ struct tfsph_ctx {
     alignas(64) unsigned char geo[sizeof(Geo<double>)];
     alignas(64) unsigned char phys[sizeof(Phys<double>)];
     NbList nbl;                 // gas neighbour list of the density pass (nbl.idx null: none)
+    XDragBufs xb;               // per-particle scratch of the ISPH / MK drag
     bool nbl_valid = false;     // nbl belongs to the current binning
     bool prepared = false;      // binning and density of the current state are done
     bool forced = false;        // ... and acc holds its pressure acceleration
@@ -412,6 +413,12 @@ int tfsph_init(tfsph_ctx **out, const tfsph_params *p, const void *const *gas, i
             }
         }
     }
+    if (p->drag != TFSPH_DRAG_IDIC) {
+        if ((rc = dalloc(c, &c->xb.g4, (size_t)n_gas * v4))) return bail(rc);
+        if ((rc = dalloc(c, &c->xb.g1, (size_t)n_gas * c->tsize))) return bail(rc);
+        if ((rc = dalloc(c, &c->xb.d4, (size_t)n_dust * v4))) return bail(rc);
+        if ((rc = dalloc(c, &c->xb.d4b, (size_t)n_dust * v4))) return bail(rc);
+    }
     c->nblk = ((int64_t)c->ncells + kScanTile - 1) / kScanTile;
     void *tmp;
     if ((rc = dalloc(c, &tmp, (size_t)c->nblk * 2 * 4))) return bail(rc);
@@ -501,8 +508,18 @@ int tfsph_step(tfsph_ctx *c, double tau, const void *t_stop, int mem_kind, const
     S.tstar_mode = c->p.tstar_mode;
     S.cell_acc = c->cell_acc;
     S.has_frozen = c->has_frozen ? 1 : 0;
-    TF_CUDA(c, launch_cell_update(L, c->geo, c->phys, c->G, c->D, c->acc, S));
-    c->launches += 1;
+    if (c->p.drag == TFSPH_DRAG_IDIC) {
+        TF_CUDA(c, launch_cell_update(L, c->geo, c->phys, c->G, c->D, c->acc, S));
+        c->launches += 1;
+    } else {
+        // the other schemes need the dust density, then the cross-phase sums and the update
+        if (c->D.n > 0) {
+            TF_CUDA(c, launch_density(L, c->geo, c->phys, c->D, c->rho_d, false, nullptr, nullptr));
+            c->launches += 1;
+        }
+        TF_CUDA(c, launch_xdrag(L, c->geo, c->phys, c->G, c->D, c->rho_g, c->rho_d, c->acc, c->xb, S, c->p.drag));
+        c->launches += 2 * ((c->G.n > 0 ? 1 : 0) + (c->D.n > 0 ? 1 : 0));
+    }
     if (ev) {
         TF_CUDA(c, cudaEventRecord(ev[TFSPH_PROF_DRAG + 1], c->stream));
         c->prof_steps += 1;
@@ -546,8 +563,9 @@ int tfsph_step_adjoint(tfsph_ctx *c, double tau, const double g[3], void *lam_gx
 {
     if (!c) return fail(nullptr, TFSPH_E_INVALID_ARG, "ctx is NULL");
     if (!std::isfinite(tau) || !(tau > 0)) return fail(c, TFSPH_E_INVALID_ARG, "tau must be finite and > 0");
-    if (c->p.eos != TFSPH_EOS_ISOTHERMAL || c->p.av_alpha > 0 || c->p.av_beta > 0)
-        return fail(c, TFSPH_E_INVALID_ARG, "the adjoint covers the isothermal gas without artificial viscosity");
+    if (c->p.eos != TFSPH_EOS_ISOTHERMAL || c->p.av_alpha > 0 || c->p.av_beta > 0 || c->p.drag != TFSPH_DRAG_IDIC)
+        return fail(c, TFSPH_E_INVALID_ARG,
+                    "the adjoint covers the isothermal gas without artificial viscosity and the IDIC drag");
     if (mem_kind != TFSPH_MEM_HOST && mem_kind != TFSPH_MEM_DEVICE) return fail(c, TFSPH_E_INVALID_ARG, "bad mem_kind");
     const int64_t ng = c->G.n, nd = c->D.n;
     if ((ng > 0 && (!lam_gx || !lam_gv)) || (nd > 0 && (!lam_dx || !lam_du || !lam_ts)))

@@ -251,6 +251,15 @@ struct StepArgs {
 };
 cudaError_t launch_cell_update(const LaunchCtx &L, const void *geo, const void *phys,
                                PhaseBufs &G, PhaseBufs &D, const void *acc, const StepArgs &S);
+// xdrag.cu: the ISPH or MK drag and particle update (scheme TFSPH_DRAG_ISPH |
+// TFSPH_DRAG_MK) after binning, gas and dust densities and the gas pressure
+// force. Scratch per particle: g4, d4, d4b (V4) and g1 (T).
+struct XDragBufs {
+    void *g4 = nullptr, *g1 = nullptr, *d4 = nullptr, *d4b = nullptr;
+};
+cudaError_t launch_xdrag(const LaunchCtx &L, const void *geo, const void *phys, PhaseBufs &G, PhaseBufs &D,
+                         const void *rho_g, const void *rho_d, const void *acc, const XDragBufs &B,
+                         const StepArgs &S, int scheme);
 cudaError_t launch_cell_adjoint(const LaunchCtx &L, const void *geo, const void *phys, PhaseBufs &G, PhaseBufs &D,
                                 const void *acc, const StepArgs &S, const void *lgx, void *lgv, const void *ldx,
                                 void *ldu, void *lA, void *lts);

@@ -62,7 +62,7 @@ def _init(params, n=4):
 
 @pytest.mark.parametrize("field,value,code", [
     ("dim", 4, 1), ("dim", 0, 1), ("h", -1.0, 1), ("cell_size", 0.0, 1), ("m_gas", 0.0, 1),
-    ("precision", 7, 1), ("eos", 5, 1), ("h", float("nan"), 2), ("reserved", 1, 1),
+    ("precision", 7, 1), ("eos", 5, 1), ("h", float("nan"), 2), ("drag", 7, 1),
 ])
 def test_init_rejects_bad_parameters_on_the_host(lib, field, value, code):
     from paper_1908_01682_gb300 import binding as b
