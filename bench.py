@@ -52,6 +52,7 @@ def parse_args(argv=None):
     ap.add_argument("--no-clocks", action="store_true")
     ap.add_argument("--no-adjoint", action="store_true")
     ap.add_argument("--no-batch", action="store_true")
+    ap.add_argument("--no-schemes", action="store_true")
     return ap.parse_args(argv)
 
 
@@ -415,6 +416,10 @@ def run_ours(args, dist: Dist):
     if not args.no_batch:
         batch = run_batch(b, args)
 
+    schemes = None
+    if not args.no_schemes:
+        schemes = run_schemes(b, args)
+
     cpu = None
     if dist.rank == 0 and dist.world == 1 and not args.no_cpu_baseline:
         cpu = cpu_baseline(args.workload, 0)
@@ -432,6 +437,7 @@ def run_ours(args, dist: Dist):
         "kernel_ms": {k: round(v, 5) for k, v in phase_avg.items()},
         "adjoint": adj,
         "batched": batch,
+        "drag_schemes": schemes,
         "cpu_baseline": cpu,
     }
     if dist.rank == 0:
@@ -558,6 +564,50 @@ def run_batch(b, args):
         "hbm_frac": (step_bytes / (batched_ms * 1e-3) / 1e9) / hbm, "hbm_peak_gbs": hbm,
         "steps": {"batched": bsteps, "looped": lsteps},
     }
+
+
+def run_schemes(b, args):
+    """The other two drag schemes of the paper on the same 3D box: ISPH
+    (Sec. 2.2) and MK (Sec. 2.1, explicit: run at tau = t_stop / 2, inside its
+    stability limit). CUDA events on the stream around 20 steps after 3."""
+    import numpy as np
+    import torch
+
+    w, desc = make_workload(args.workload)
+    f32 = lambda a: None if a is None else np.ascontiguousarray(a, dtype=np.float32)
+    stream = torch.cuda.current_stream()
+    cell_acc = b.TFSPH_CELL_ACC_FP32 if args.cell_acc == "fp32" else b.TFSPH_CELL_ACC_FP64
+    out = {}
+    for name, drag in (("isph", b.TFSPH_DRAG_ISPH), ("mk", b.TFSPH_DRAG_MK)):
+        tau = w.tau if drag == b.TFSPH_DRAG_ISPH else 0.5 * float(np.min(w.tstop))
+        p = b.params_from_dict(w.params, cell_acc=cell_acc, drag=drag)
+        with b.Context(p, f32(w.gx), f32(w.gv), f32(w.dx), f32(w.du), f32(w.tstop), ge=f32(w.ge),
+                       frozen=w.frozen) as c:
+            c.set_stream(stream)
+            for _ in range(3):
+                c.step(tau, w.g)
+            torch.cuda.synchronize()
+            e0 = torch.cuda.Event(enable_timing=True)
+            e1 = torch.cuda.Event(enable_timing=True)
+            steps = 20
+            e0.record(stream)
+            for _ in range(steps):
+                c.step(tau, w.g)
+            e1.record(stream)
+            torch.cuda.synchronize()
+            c.sync()
+            ms = e0.elapsed_time(e1) / steps
+            c.profile(True)
+            for _ in range(5):
+                c.step(tau, w.g)
+            ph, ps, _ = c.profile_read()
+            c.profile(False)
+        n = w.n_gas + w.n_dust
+        out[name] = {"ms_per_step": ms, "value": n / (ms * 1e-3), "unit": UNIT, "tau": tau,
+                     "drag_phase_ms": ph["drag"] / max(1, ps),
+                     "note": "drag phase = cross-phase sums + particle update (+ dust density for ISPH)"}
+    out["workload"] = desc
+    return out
 
 
 def run_e2e(b, ctx, w, args, dist):

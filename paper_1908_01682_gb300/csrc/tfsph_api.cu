@@ -512,8 +512,9 @@ int tfsph_step(tfsph_ctx *c, double tau, const void *t_stop, int mem_kind, const
         TF_CUDA(c, launch_cell_update(L, c->geo, c->phys, c->G, c->D, c->acc, S));
         c->launches += 1;
     } else {
-        // the other schemes need the dust density, then the cross-phase sums and the update
-        if (c->D.n > 0) {
+        // ISPH needs the dust density (its interpolations divide by it); both
+        // schemes then run the cross-phase sums and the update
+        if (c->D.n > 0 && c->p.drag == TFSPH_DRAG_ISPH) {
             TF_CUDA(c, launch_density(L, c->geo, c->phys, c->D, c->rho_d, false, nullptr, nullptr));
             c->launches += 1;
         }
