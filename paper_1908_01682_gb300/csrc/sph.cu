@@ -146,6 +146,8 @@ __device__ __forceinline__ void walk_smem_range(PairAcc<T, MODE> &A, const Geo<T
                                                 const V4<T> &pa, const V4<T> *spos, const V4<T> *svel,
                                                 const T *srho, const uint32_t *sid, int j0, int j1, NbRec *rec)
 {
+    // a row holds a few candidates: no unrolled prologue or remainder
+#pragma unroll 1
     for (int j = j0; j < j1; ++j) {
         const V4<T> pb = spos[j];
         T d[3];
@@ -164,6 +166,10 @@ __device__ __forceinline__ void walk_smem_range(PairAcc<T, MODE> &A, const Geo<T
         }
     }
 }
+
+// floor(x) as an int, in one conversion (x is a small cell offset).
+__device__ __forceinline__ int floor_int(float x) { return __float2int_rd(x); }
+__device__ __forceinline__ int floor_int(double x) { return __double2int_rd(x); }
 
 // Candidate walk of one owned particle over the staged tile (REC: the
 // density pass recording the neighbour list).
@@ -210,8 +216,8 @@ __device__ __forceinline__ void walk_tile(PairAcc<T, MODE> &A, const Geo<T> &G, 
             // x window: the cells whose slab lies within t = sqrt(rem)/w of the
             // particle, (o - fx) <= t for o > 0 and (fx + |o| - 1) <= t for o < 0
             const T t = approx_sqrt(G.lim2 - dz2 - dy2) * G.inv_w[0];
-            const int ohi = min(G.R[0], max(0, (int)floor(fx + t)));
-            const int olo = -min(G.R[0], max(0, (int)floor(t - fx + T(1))));
+            const int ohi = min(G.R[0], max(0, floor_int(fx + t)));
+            const int olo = -min(G.R[0], max(0, floor_int(t - fx + T(1))));
             const int hrow = C.H[0] * ((hy + oy) + C.H[1] * (hz + oz));
             const int u0 = hx + olo, u1 = hx + ohi + 1;  // halo x cells [u0, u1)
             // [u0, a0) across the low seam, [a0, a1) inside, [a1, u1) across the high seam
