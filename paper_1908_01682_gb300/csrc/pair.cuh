@@ -130,7 +130,7 @@ template <class T, int MODE> struct PairAcc {
             return;
         }
         if (MODE <= 1) {
-            sum += kernel_w(G, approx_sqrt(r2) * G.inv_h);
+            sum += kernel_w4(approx_sqrt(r2) * G.inv_h);
             if (MODE == 1) {
                 ++cnt;
                 fp += (uint64_t)((idb & kIdMask) + 1u) * 0x9E3779B97F4A7C15ull;
@@ -214,7 +214,7 @@ __device__ __forceinline__ void acc_store(const PairAcc<T, MODE> &A, const Phys<
         return;
     }
     if (MODE <= 1) {
-        const T r = mass * A.sum;
+        const T r = (mass * Ph.wnorm4) * A.sum;
         out_rho[a] = r;
         if (pr_out) {
             const T pr = Ph.eos == TFSPH_EOS_ADIABATIC ? Ph.gm1 * vel[a].w / r : Ph.cs2 / r;

@@ -79,6 +79,7 @@ template <class T> struct Phys {
     T av_alpha, av_beta;
     T eta2;           // 0.01 h^2
     T h;
+    T wnorm4;         // sigma_d / h^d / 4: the density sums accumulate 4 W / (sigma_d / h^d)
     int eos;
     int av;
 };
@@ -237,6 +238,7 @@ void make_geo_phys(const tfsph_params &p, const int ncell[3], uint32_t ncells, G
     Ph.av_beta = T(p.av_beta);
     Ph.eta2 = T(0.01 * p.h * p.h);
     Ph.h = T(p.h);
+    Ph.wnorm4 = T(0.25 * sigma / pow(p.h, p.dim));
     Ph.eos = p.eos;
     Ph.av = (p.av_alpha > 0.0 || p.av_beta > 0.0) ? 1 : 0;
 }
@@ -342,6 +344,15 @@ template <class T> __device__ __forceinline__ T kernel_w(const Geo<T> &G, T q)
     const T inner = T(1) + q * q * (T(-1.5) + T(0.75) * q);
     const T outer = T(0.25) * a * a * a;
     return G.wnorm * (q < T(1) ? inner : outer);
+}
+
+// 4 W / (sigma_d / h^d): the density sums add this and scale once at the end
+//   (q < 1 ? 4 - 6 q^2 + 3 q^3 : (2 - q)^3)
+template <class T> __device__ __forceinline__ T kernel_w4(T q)
+{
+    const T a = fmax(T(2) - q, T(0));
+    const T inner = T(4) + q * q * (T(-6) + T(3) * q);
+    return q < T(1) ? inner : a * a * a;
 }
 
 template <class T> __device__ __forceinline__ T kernel_f(const Geo<T> &G, T q, T inv_q)
