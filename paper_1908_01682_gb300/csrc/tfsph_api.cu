@@ -127,15 +127,43 @@ LaunchCtx lctx(const tfsph_ctx *c)
     return L;
 }
 
-// Device copies of user arrays: returns device pointers (host input is staged).
+// Device address of a page-locked (registered) host buffer, through which
+// kernels read or write it directly over the host link; NULL for pageable
+// memory, which goes through the staging buffer.
+void *mapped_host(const void *p)
+{
+    cudaPointerAttributes a{};
+    if (cudaPointerGetAttributes(&a, p) != cudaSuccess) {
+        cudaGetLastError();
+        return nullptr;
+    }
+    return (a.type == cudaMemoryTypeHost && a.devicePointer) ? a.devicePointer : nullptr;
+}
+
+// Device copies of user arrays: returns device pointers (host input is
+// staged, unless every array is page-locked: then kernels read it in place
+// and *staged stays false).
 int stage_inputs(tfsph_ctx *c, const void *const *arrs, int narr, int64_t n, const uint8_t *frozen, int mem_kind,
-                 std::vector<const void *> &dev, const uint8_t **dev_frozen)
+                 std::vector<const void *> &dev, const uint8_t **dev_frozen, bool *staged = nullptr)
 {
     dev.assign(narr, nullptr);
     *dev_frozen = nullptr;
+    if (staged) *staged = false;
     if (n == 0) return TFSPH_OK;
     for (int k = 0; k < narr; ++k)
         if (!arrs[k]) return fail(c, TFSPH_E_INVALID_ARG, "NULL input array");
+    if (mem_kind == TFSPH_MEM_HOST) {
+        std::vector<const void *> mapped(narr, nullptr);
+        bool all = true;
+        for (int k = 0; k < narr && all; ++k) all = (mapped[k] = mapped_host(arrs[k])) != nullptr;
+        const uint8_t *mf = nullptr;
+        if (all && frozen) all = (mf = static_cast<const uint8_t *>(mapped_host(frozen))) != nullptr;
+        if (all) {
+            dev = mapped;
+            *dev_frozen = mf;
+            return TFSPH_OK;
+        }
+    }
     if (mem_kind == TFSPH_MEM_DEVICE) {
         for (int k = 0; k < narr; ++k) dev[k] = arrs[k];
         *dev_frozen = frozen;
@@ -143,6 +171,7 @@ int stage_inputs(tfsph_ctx *c, const void *const *arrs, int narr, int64_t n, con
     }
     const size_t need = (size_t)narr * (size_t)n * c->tsize + (frozen ? (size_t)n + 256 : 0);
     if (need > c->staging_bytes) return fail(c, TFSPH_E_INTERNAL, "staging buffer too small");
+    if (staged) *staged = true;
     char *base = static_cast<char *>(c->staging);
     for (int k = 0; k < narr; ++k) {
         char *dst = base + (size_t)k * (size_t)n * c->tsize;
@@ -168,12 +197,13 @@ int load_state(tfsph_ctx *c, const void *const *gas, const void *const *dust, co
     LaunchCtx L = lctx(c);
     std::vector<const void *> dv;
     const uint8_t *dfz = nullptr;
-    int rc = stage_inputs(c, gas, ngas_arr, c->G.n, frozen, mem_kind, dv, &dfz);
+    bool staged = false;
+    int rc = stage_inputs(c, gas, ngas_arr, c->G.n, frozen, mem_kind, dv, &dfz, &staged);
     if (rc) return rc;
     c->G.cur = 0;
     TF_CUDA(c, launch_pack(L, c->G, dv.data(), c->p.eos == TFSPH_EOS_ADIABATIC, dfz, true));
     // the gas staging area is reused for dust only after the pack has consumed it
-    if (mem_kind == TFSPH_MEM_HOST) TF_CUDA(c, cudaStreamSynchronize(c->stream));
+    if (staged) TF_CUDA(c, cudaStreamSynchronize(c->stream));
     rc = stage_inputs(c, dust, ndust_arr, c->D.n, nullptr, mem_kind, dv, &dfz);
     if (rc) return rc;
     c->D.cur = 0;
@@ -833,6 +863,14 @@ int tfsph_fields(tfsph_ctx *c, int field, void *out, int mem_kind, int order)
     if (P->n == 0) return TFSPH_OK;
     if (!out) return fail(c, TFSPH_E_INVALID_ARG, "out is NULL");
     const size_t bytes = (size_t)ncomp * (size_t)P->n * c->tsize;
+    if (mem_kind == TFSPH_MEM_HOST) {
+        // a page-locked host buffer is written by the kernel directly
+        if (void *m = mapped_host(out)) {
+            TF_CUDA(c, launch_unpack(L, *P, what, m, order, aux));
+            TF_CUDA(c, cudaStreamSynchronize(c->stream));
+            return TFSPH_OK;
+        }
+    }
     void *dst = mem_kind == TFSPH_MEM_DEVICE ? out : c->staging;
     if (mem_kind == TFSPH_MEM_HOST && bytes > c->staging_bytes) return fail(c, TFSPH_E_INTERNAL, "staging too small");
     TF_CUDA(c, launch_unpack(L, *P, what, dst, order, aux));

@@ -325,3 +325,43 @@ def test_step_adjoint_after_load_reuses_forward_quantities(orc):
             outs.append([t.cpu().numpy() for t in lam + [lts]])
     for a, r in zip(outs[1], outs[0]):
         assert np.array_equal(a, r)
+
+
+def test_page_locked_host_buffers_match_pageable(orc):
+    """set_state and fields with page-locked host buffers (read and written by
+    the kernels in place) give exactly what pageable buffers (staged) give."""
+    torch = pytest.importorskip("torch")
+    b = gpu_lib()
+    w = workloads.column2d(nside=20, precision=0)
+
+    def pinned(a):
+        t = torch.empty(a.shape, dtype=torch.float32, pin_memory=True)
+        t.numpy()[...] = a
+        return t
+
+    fz = torch.empty(w.frozen.shape, dtype=torch.uint8, pin_memory=True)
+    fz.numpy()[...] = w.frozen
+    keep = [pinned(a) for a in (w.gx, w.gv, w.dx, w.du, w.tstop)]
+    outs = {}
+    for mode in ("pageable", "pinned"):
+        with gpu_context(w) as c:
+            if mode == "pinned":
+                c.set_state(*[t.numpy() for t in keep], frozen=fz.numpy())
+            else:
+                c.set_state(*[np.ascontiguousarray(a, np.float32) for a in (w.gx, w.gv, w.dx, w.du, w.tstop)],
+                            frozen=w.frozen)
+            c.step(w.tau, w.g)
+            res = []
+            for f in (b.TFSPH_FIELD_POS_G, b.TFSPH_FIELD_VEL_G, b.TFSPH_FIELD_POS_D, b.TFSPH_FIELD_VEL_D,
+                      b.TFSPH_FIELD_RHO_G):
+                n = w.n_gas if f in (b.TFSPH_FIELD_POS_G, b.TFSPH_FIELD_VEL_G, b.TFSPH_FIELD_RHO_G) else w.n_dust
+                shape = (n,) if f == b.TFSPH_FIELD_RHO_G else (w.dim, n)
+                if mode == "pinned":
+                    t = torch.empty(shape, dtype=torch.float32, pin_memory=True)
+                    c.field(f, out=t.numpy())
+                    res.append(t.numpy().copy())
+                else:
+                    res.append(c.field(f))
+            outs[mode] = res
+    for a, r in zip(outs["pinned"], outs["pageable"]):
+        assert np.array_equal(a, r)
