@@ -205,7 +205,8 @@ int tfsph_step_adjoint(tfsph_ctx *c, double tau, const double g[3], void *lam_gx
  * from the update (this is what makes a checkpointed reverse pass cost one
  * force evaluation per step). tfsph_state_bytes gives the size; save and
  * load copy to/from a caller-owned buffer of mem_kind (device copies are
- * asynchronous on the context's stream; host copies synchronise). A snapshot
+ * asynchronous on the context's stream, one kernel launch, and need a
+ * 4-byte-aligned buffer; host copies synchronise). A snapshot
  * loads only into a context of the same counts, dimension, precision and
  * cell grid: INVALID_ARG from a host buffer; for a device buffer the header
  * is checked on the device and a mismatch is reported by the next

@@ -278,48 +278,78 @@ __global__ void __launch_bounds__(256) k_max_final(const T *__restrict__ partial
 }
 
 // Adjoint vectors: component-major id order <-> V4 storage order.
+// All adjoint inputs of a step into storage order in one launch (gas x, v;
+// dust x, u), and the dust t_stop adjoint scratch cleared.
 template <class T>
-__global__ void k_lam_gather(const uint32_t *__restrict__ id, int n, int dim, const T *__restrict__ lam,
-                             V4<T> *__restrict__ out)
+__global__ void k_lam_gather_all(const uint32_t *__restrict__ gid, int ng, const uint32_t *__restrict__ did, int nd,
+                                 int dim, const T *__restrict__ lgx, const T *__restrict__ lgv,
+                                 const T *__restrict__ ldx, const T *__restrict__ ldu, V4<T> *__restrict__ gx4,
+                                 V4<T> *__restrict__ gv4, V4<T> *__restrict__ dx4, V4<T> *__restrict__ du4,
+                                 T *__restrict__ lts)
 {
-    const int s = blockIdx.x * blockDim.x + threadIdx.x;
-    if (s >= n) return;
-    const size_t i = id[s] & kIdMask;
-    V4<T> v;
-    v.x = lam[i];
-    v.y = dim > 1 ? lam[(size_t)n + i] : T(0);
-    v.z = dim > 2 ? lam[2 * (size_t)n + i] : T(0);
-    v.w = T(0);
-    out[s] = v;
-}
-
-template <class T>
-__global__ void k_lam_scatter(const uint32_t *__restrict__ id, int n, int dim, const V4<T> *__restrict__ a,
-                              const V4<T> *__restrict__ b, T *__restrict__ lam)
-{
-    const int s = blockIdx.x * blockDim.x + threadIdx.x;
-    if (s >= n) return;
-    const size_t i = id[s] & kIdMask;
-    V4<T> v = a[s];
-    if (b) {
-        const V4<T> w = b[s];
-        v.x += w.x;
-        v.y += w.y;
-        v.z += w.z;
+    const int t = blockIdx.x * blockDim.x + threadIdx.x;
+    const bool gas = t < ng;
+    const int s = gas ? t : t - ng;
+    const int n = gas ? ng : nd;
+    if (!gas && s >= nd) return;
+    const size_t i = (gas ? gid[s] : did[s]) & kIdMask;
+    const T *la = gas ? lgx : ldx;
+    const T *lb = gas ? lgv : ldu;
+    V4<T> a, b;
+    a.x = la[i];
+    b.x = lb[i];
+    a.y = dim > 1 ? la[(size_t)n + i] : T(0);
+    b.y = dim > 1 ? lb[(size_t)n + i] : T(0);
+    a.z = dim > 2 ? la[2 * (size_t)n + i] : T(0);
+    b.z = dim > 2 ? lb[2 * (size_t)n + i] : T(0);
+    a.w = b.w = T(0);
+    if (gas) {
+        gx4[s] = a;
+        gv4[s] = b;
+    } else {
+        dx4[s] = a;
+        du4[s] = b;
+        lts[s] = T(0);
     }
-    lam[i] = v.x;
-    if (dim > 1) lam[(size_t)n + i] = v.y;
-    if (dim > 2) lam[2 * (size_t)n + i] = v.z;
 }
 
-// lambda_t (id order) += lambda_t (storage order)
+// All adjoint outputs of a step back to id order in one launch: gas
+// lambda_x = gx4 + out (.xyz), lambda_v = gv4; dust lambda_u = du4 and
+// lambda_t_stop += lts.
 template <class T>
-__global__ void k_lam_add_scalar(const uint32_t *__restrict__ id, int n, const T *__restrict__ src,
-                                 T *__restrict__ dst)
+__global__ void k_lam_scatter_all(const uint32_t *__restrict__ gid, int ng, const uint32_t *__restrict__ did, int nd,
+                                  int dim, const V4<T> *__restrict__ gx4, const V4<T> *__restrict__ out,
+                                  const V4<T> *__restrict__ gv4, const V4<T> *__restrict__ du4,
+                                  const T *__restrict__ lts, T *__restrict__ lgx, T *__restrict__ lgv,
+                                  T *__restrict__ ldu, T *__restrict__ lt)
 {
-    const int s = blockIdx.x * blockDim.x + threadIdx.x;
-    if (s >= n) return;
-    dst[id[s] & kIdMask] += src[s];
+    const int t = blockIdx.x * blockDim.x + threadIdx.x;
+    if (t < ng) {
+        const size_t i = gid[t] & kIdMask;
+        V4<T> x = gx4[t];
+        const V4<T> o = out[t], v = gv4[t];
+        x.x += o.x;
+        x.y += o.y;
+        x.z += o.z;
+        lgx[i] = x.x;
+        lgv[i] = v.x;
+        if (dim > 1) {
+            lgx[(size_t)ng + i] = x.y;
+            lgv[(size_t)ng + i] = v.y;
+        }
+        if (dim > 2) {
+            lgx[2 * (size_t)ng + i] = x.z;
+            lgv[2 * (size_t)ng + i] = v.z;
+        }
+    } else if (t < ng + nd) {
+        const int s = t - ng;
+        const size_t i = did[s] & kIdMask;
+        const V4<T> u = du4[s];
+        ldu[i] = u.x;
+        if (dim > 1) ldu[(size_t)nd + i] = u.y;
+        if (dim > 2) ldu[2 * (size_t)nd + i] = u.z;
+        lt[i] += lts[s];
+    }
 }
 
 // lambda_rho = dq/drho lambda_q with q = cs^2 / rho (isothermal): -cs^2/rho^2 lambda_q
@@ -504,47 +534,44 @@ cudaError_t launch_max_speed(const LaunchCtx &L, const void *phys, const PhaseBu
                                      : max_speed_t<float>(L, phys, G, partials, nblk, result);
 }
 
-cudaError_t launch_lam_gather(const LaunchCtx &L, const PhaseBufs &P, const void *lam, void *out)
+cudaError_t launch_lam_gather_all(const LaunchCtx &L, const PhaseBufs &G, const PhaseBufs &D, const void *lgx,
+                                  const void *lgv, const void *ldx, const void *ldu, void *gx4, void *gv4, void *dx4,
+                                  void *du4, void *lts)
 {
-    if (P.n == 0) return cudaSuccess;
-    const int n = (int)P.n;
+    const int ng = (int)G.n, nd = (int)D.n;
+    if (ng + nd == 0) return cudaSuccess;
     if (L.precision == TFSPH_FP64)
-        k_lam_gather<double><<<grid_for(n, 256), 256, 0, L.stream>>>(P.id[P.cur], n, L.dim,
-                                                                     static_cast<const double *>(lam),
-                                                                     static_cast<double4a *>(out));
+        k_lam_gather_all<double><<<grid_for(ng + nd, 256), 256, 0, L.stream>>>(
+            G.id[G.cur], ng, D.id[D.cur], nd, L.dim, static_cast<const double *>(lgx), static_cast<const double *>(lgv),
+            static_cast<const double *>(ldx), static_cast<const double *>(ldu), static_cast<double4a *>(gx4),
+            static_cast<double4a *>(gv4), static_cast<double4a *>(dx4), static_cast<double4a *>(du4),
+            static_cast<double *>(lts));
     else
-        k_lam_gather<float><<<grid_for(n, 256), 256, 0, L.stream>>>(P.id[P.cur], n, L.dim, static_cast<const float *>(lam),
-                                                                    static_cast<float4 *>(out));
+        k_lam_gather_all<float><<<grid_for(ng + nd, 256), 256, 0, L.stream>>>(
+            G.id[G.cur], ng, D.id[D.cur], nd, L.dim, static_cast<const float *>(lgx), static_cast<const float *>(lgv),
+            static_cast<const float *>(ldx), static_cast<const float *>(ldu), static_cast<float4 *>(gx4),
+            static_cast<float4 *>(gv4), static_cast<float4 *>(dx4), static_cast<float4 *>(du4),
+            static_cast<float *>(lts));
     return cudaGetLastError();
 }
 
-cudaError_t launch_lam_scatter(const LaunchCtx &L, const PhaseBufs &P, const void *a, const void *b, void *lam)
+cudaError_t launch_lam_scatter_all(const LaunchCtx &L, const PhaseBufs &G, const PhaseBufs &D, const void *gx4,
+                                   const void *out, const void *gv4, const void *du4, const void *lts, void *lgx,
+                                   void *lgv, void *ldu, void *lt)
 {
-    if (P.n == 0) return cudaSuccess;
-    const int n = (int)P.n;
+    const int ng = (int)G.n, nd = (int)D.n;
+    if (ng + nd == 0) return cudaSuccess;
     if (L.precision == TFSPH_FP64)
-        k_lam_scatter<double><<<grid_for(n, 256), 256, 0, L.stream>>>(
-            P.id[P.cur], n, L.dim, static_cast<const double4a *>(a), static_cast<const double4a *>(b),
-            static_cast<double *>(lam));
+        k_lam_scatter_all<double><<<grid_for(ng + nd, 256), 256, 0, L.stream>>>(
+            G.id[G.cur], ng, D.id[D.cur], nd, L.dim, static_cast<const double4a *>(gx4),
+            static_cast<const double4a *>(out), static_cast<const double4a *>(gv4), static_cast<const double4a *>(du4),
+            static_cast<const double *>(lts), static_cast<double *>(lgx), static_cast<double *>(lgv),
+            static_cast<double *>(ldu), static_cast<double *>(lt));
     else
-        k_lam_scatter<float><<<grid_for(n, 256), 256, 0, L.stream>>>(P.id[P.cur], n, L.dim,
-                                                                     static_cast<const float4 *>(a),
-                                                                     static_cast<const float4 *>(b),
-                                                                     static_cast<float *>(lam));
-    return cudaGetLastError();
-}
-
-cudaError_t launch_lam_add_scalar(const LaunchCtx &L, const PhaseBufs &P, const void *src, void *dst)
-{
-    if (P.n == 0) return cudaSuccess;
-    const int n = (int)P.n;
-    if (L.precision == TFSPH_FP64)
-        k_lam_add_scalar<double><<<grid_for(n, 256), 256, 0, L.stream>>>(P.id[P.cur], n,
-                                                                         static_cast<const double *>(src),
-                                                                         static_cast<double *>(dst));
-    else
-        k_lam_add_scalar<float><<<grid_for(n, 256), 256, 0, L.stream>>>(P.id[P.cur], n, static_cast<const float *>(src),
-                                                                        static_cast<float *>(dst));
+        k_lam_scatter_all<float><<<grid_for(ng + nd, 256), 256, 0, L.stream>>>(
+            G.id[G.cur], ng, D.id[D.cur], nd, L.dim, static_cast<const float4 *>(gx4), static_cast<const float4 *>(out),
+            static_cast<const float4 *>(gv4), static_cast<const float4 *>(du4), static_cast<const float *>(lts),
+            static_cast<float *>(lgx), static_cast<float *>(lgv), static_cast<float *>(ldu), static_cast<float *>(lt));
     return cudaGetLastError();
 }
 

@@ -644,11 +644,8 @@ int tfsph_step_adjoint(tfsph_ctx *c, double tau, const double g[3], void *lam_gx
     // forward quantities of the step: binning, density, pressure acceleration
     if ((rc = forward_quantities(c))) return rc;
     // adjoint vectors into storage order
-    TF_CUDA(c, launch_lam_gather(L, c->G, dgx, c->adj_gx4));
-    TF_CUDA(c, launch_lam_gather(L, c->G, dgv, c->adj_gv4));
-    TF_CUDA(c, launch_lam_gather(L, c->D, ddx, c->adj_dx4));
-    TF_CUDA(c, launch_lam_gather(L, c->D, ddu, c->adj_du4));
-    if (nd > 0) TF_CUDA(c, cudaMemsetAsync(c->adj_lts, 0, bt, c->stream));
+    TF_CUDA(c, launch_lam_gather_all(L, c->G, c->D, dgx, dgv, ddx, ddu, c->adj_gx4, c->adj_gv4, c->adj_dx4,
+                                     c->adj_du4, c->adj_lts));
     StepArgs S;
     S.tau = tau;
     S.g[0] = gg[0];
@@ -665,13 +662,10 @@ int tfsph_step_adjoint(tfsph_ctx *c, double tau, const double g[3], void *lam_gx
         TF_CUDA(c, launch_force_adjoint(L, c->geo, c->phys, c->G, c->adj_lA, c->adj_out));
         TF_CUDA(c, launch_lamq_to_lamrho(L, c->G, c->adj_out, c->rho_g, c->p.cs * c->p.cs, c->adj_lrho));
         TF_CUDA(c, launch_density_adjoint(L, c->geo, c->phys, c->G, c->adj_lrho, c->adj_out));
-        TF_CUDA(c, launch_lam_scatter(L, c->G, c->adj_gx4, c->adj_out, dgx));
-        TF_CUDA(c, launch_lam_scatter(L, c->G, c->adj_gv4, nullptr, dgv));
     }
-    if (nd > 0) {
-        TF_CUDA(c, launch_lam_scatter(L, c->D, c->adj_du4, nullptr, ddu));
-        TF_CUDA(c, launch_lam_add_scalar(L, c->D, c->adj_lts, dts));
-    }
+    // lambda_x (+ the pair terms), lambda_v, lambda_u and lambda_t_stop back to id order
+    TF_CUDA(c, launch_lam_scatter_all(L, c->G, c->D, c->adj_gx4, c->adj_out, c->adj_gv4, c->adj_du4, c->adj_lts, dgx,
+                                      dgv, ddu, dts));
     if (mem_kind == TFSPH_MEM_HOST) {
         if (ng > 0) {
             TF_CUDA(c, cudaMemcpyAsync(lam_gx, dgx, bg, cudaMemcpyDeviceToHost, c->stream));
@@ -715,6 +709,33 @@ struct SnapPart {
     size_t bytes;
 };
 
+// One launch copies every part of a device snapshot (word by word: every
+// part size and offset is a multiple of 4 bytes) and, when saving, writes the
+// header, instead of one copy call per array.
+constexpr int kCopyParts = 12;
+constexpr int kHeaderWords = (int)(sizeof(SnapHeader) / 4);
+static_assert(sizeof(SnapHeader) % 4 == 0, "snapshot header is copied in words");
+struct CopyList {
+    const uint32_t *src[kCopyParts];
+    uint32_t *dst[kCopyParts];
+    uint64_t words[kCopyParts];
+    int n;
+    uint32_t head[kHeaderWords];
+    uint32_t *head_dst;  // NULL: no header to write
+};
+
+__global__ void __launch_bounds__(256) k_copy_words(CopyList L)
+{
+    if (L.head_dst && blockIdx.x == 0 && threadIdx.x < kHeaderWords) L.head_dst[threadIdx.x] = L.head[threadIdx.x];
+    const uint64_t t = (uint64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    const uint64_t stride = (uint64_t)gridDim.x * blockDim.x;
+    for (int s = 0; s < L.n; ++s) {
+        const uint32_t *__restrict__ src = L.src[s];
+        uint32_t *__restrict__ dst = L.dst[s];
+        for (uint64_t i = t; i < L.words[s]; i += stride) dst[i] = src[i];
+    }
+}
+
 std::vector<SnapPart> snap_parts(tfsph_ctx *c)
 {
     const size_t v4 = 4 * c->tsize, nc = (size_t)c->ncells + 1;
@@ -757,16 +778,34 @@ int tfsph_save_state(tfsph_ctx *c, void *buf, int mem_kind)
     h.dim = c->dim;
     h.precision = c->precision;
     h.ncells = c->ncells;
-    const cudaMemcpyKind k = mem_kind == TFSPH_MEM_DEVICE ? cudaMemcpyDeviceToDevice : cudaMemcpyDeviceToHost;
     char *dst = static_cast<char *>(buf);
-    if (mem_kind == TFSPH_MEM_DEVICE) TF_CUDA(c, cudaMemcpyAsync(dst, &h, sizeof h, cudaMemcpyHostToDevice, c->stream));
-    else memcpy(dst, &h, sizeof h);
+    if (mem_kind == TFSPH_MEM_DEVICE) {
+        if (reinterpret_cast<uintptr_t>(buf) % 4 != 0) return fail(c, TFSPH_E_INVALID_ARG, "buf must be 4-byte aligned");
+        CopyList L{};
+        memcpy(L.head, &h, sizeof h);
+        L.head_dst = reinterpret_cast<uint32_t *>(dst);
+        dst += sizeof h;
+        for (const SnapPart &q : snap_parts(c)) {
+            if (q.bytes) {
+                L.src[L.n] = static_cast<const uint32_t *>(q.ptr);
+                L.dst[L.n] = reinterpret_cast<uint32_t *>(dst);
+                L.words[L.n] = q.bytes / 4;
+                ++L.n;
+            }
+            dst += q.bytes;
+        }
+        k_copy_words<<<4 * 152, 256, 0, c->stream>>>(L);
+        TF_CUDA(c, cudaGetLastError());
+        c->launches += 1;
+        return TFSPH_OK;
+    }
+    memcpy(dst, &h, sizeof h);
     dst += sizeof h;
     for (const SnapPart &q : snap_parts(c)) {
-        if (q.bytes) TF_CUDA(c, cudaMemcpyAsync(dst, q.ptr, q.bytes, k, c->stream));
+        if (q.bytes) TF_CUDA(c, cudaMemcpyAsync(dst, q.ptr, q.bytes, cudaMemcpyDeviceToHost, c->stream));
         dst += q.bytes;
     }
-    if (mem_kind == TFSPH_MEM_HOST) TF_CUDA(c, cudaStreamSynchronize(c->stream));  // complete on return
+    TF_CUDA(c, cudaStreamSynchronize(c->stream));  // complete on return
     return TFSPH_OK;
 }
 
@@ -792,11 +831,27 @@ int tfsph_load_state(tfsph_ctx *c, const void *buf, int mem_kind)
             h.precision != c->precision || h.ncells != c->ncells)
             return fail(c, TFSPH_E_INVALID_ARG, "snapshot does not belong to a context of this shape");
     }
-    const cudaMemcpyKind k = mem_kind == TFSPH_MEM_DEVICE ? cudaMemcpyDeviceToDevice : cudaMemcpyHostToDevice;
     src += sizeof h;
-    for (const SnapPart &q : snap_parts(c)) {
-        if (q.bytes) TF_CUDA(c, cudaMemcpyAsync(q.ptr, src, q.bytes, k, c->stream));
-        src += q.bytes;
+    if (mem_kind == TFSPH_MEM_DEVICE) {
+        if (reinterpret_cast<uintptr_t>(buf) % 4 != 0) return fail(c, TFSPH_E_INVALID_ARG, "buf must be 4-byte aligned");
+        CopyList L{};
+        for (const SnapPart &q : snap_parts(c)) {
+            if (q.bytes) {
+                L.src[L.n] = reinterpret_cast<const uint32_t *>(src);
+                L.dst[L.n] = static_cast<uint32_t *>(q.ptr);
+                L.words[L.n] = q.bytes / 4;
+                ++L.n;
+            }
+            src += q.bytes;
+        }
+        k_copy_words<<<4 * 152, 256, 0, c->stream>>>(L);
+        TF_CUDA(c, cudaGetLastError());
+        c->launches += 1;
+    } else {
+        for (const SnapPart &q : snap_parts(c)) {
+            if (q.bytes) TF_CUDA(c, cudaMemcpyAsync(q.ptr, src, q.bytes, cudaMemcpyHostToDevice, c->stream));
+            src += q.bytes;
+        }
     }
     if (mem_kind == TFSPH_MEM_HOST) TF_CUDA(c, cudaStreamSynchronize(c->stream));
     // the cell keys are rewritten by the step's update before the next binning;

@@ -148,9 +148,14 @@ cudaError_t launch_check(const LaunchCtx &L, const void *geo, const PhaseBufs &P
 cudaError_t launch_max_speed(const LaunchCtx &L, const void *phys, const PhaseBufs &G,
                              void *partials, int nblk, void *result);
 cudaError_t launch_debug_keys(const LaunchCtx &L, const void *geo, const PhaseBufs &P, uint32_t *out);
-cudaError_t launch_lam_gather(const LaunchCtx &L, const PhaseBufs &P, const void *lam, void *out);
-cudaError_t launch_lam_scatter(const LaunchCtx &L, const PhaseBufs &P, const void *a, const void *b, void *lam);
-cudaError_t launch_lam_add_scalar(const LaunchCtx &L, const PhaseBufs &P, const void *src, void *dst);
+// One launch each for all adjoint arrays of a step: into storage order (and
+// lts cleared), and back to id order.
+cudaError_t launch_lam_gather_all(const LaunchCtx &L, const PhaseBufs &G, const PhaseBufs &D, const void *lgx,
+                                  const void *lgv, const void *ldx, const void *ldu, void *gx4, void *gv4, void *dx4,
+                                  void *du4, void *lts);
+cudaError_t launch_lam_scatter_all(const LaunchCtx &L, const PhaseBufs &G, const PhaseBufs &D, const void *gx4,
+                                   const void *out, const void *gv4, const void *du4, const void *lts, void *lgx,
+                                   void *lgv, void *ldu, void *lt);
 cudaError_t launch_lamq_to_lamrho(const LaunchCtx &L, const PhaseBufs &P, const void *lq, const void *rho, double cs2,
                                   void *lrho);
 
