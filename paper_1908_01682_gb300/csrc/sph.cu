@@ -370,17 +370,25 @@ k_pair_tile(Geo<T> G, Phys<T> Ph, TileCfg C, const V4<T> *__restrict__ pos, cons
                                                  : pair_r2<T, DIM, false>(G, pa, pb, d);
                     A.add(G, Ph, pb, nullptr, T(1), 0u, r2, d);
                 };
-                // entries in groups of 8 independent loads, so one memory
-                // latency covers eight pairs
+                // entries in groups of 8 independent loads through the read-only
+                // path, the next group loaded while the current one is used
                 int q = 0;
-                for (; q + 8 <= n; q += 8) {
-                    uint32_t ent[8];
+                uint32_t ent[8], nxt[8];
+                if (n >= 8) {
 #pragma unroll
-                    for (int u = 0; u < 8; ++u) ent[u] = e[(size_t)(q + u) * st];
+                    for (int u = 0; u < 8; ++u) nxt[u] = __ldg(&e[(size_t)u * st]);
+                }
+                for (; q + 8 <= n; q += 8) {
+#pragma unroll
+                    for (int u = 0; u < 8; ++u) ent[u] = nxt[u];
+                    if (q + 16 <= n) {
+#pragma unroll
+                        for (int u = 0; u < 8; ++u) nxt[u] = __ldg(&e[(size_t)(q + 8 + u) * st]);
+                    }
 #pragma unroll
                     for (int u = 0; u < 8; ++u) pair(ent[u]);
                 }
-                for (; q < n; ++q) pair(e[(size_t)q * st]);
+                for (; q < n; ++q) pair(__ldg(&e[(size_t)q * st]));
             } else {
                 walk_tile<T, DIM, MODE, false>(A, G, Ph, C, c0, pa, lstart, spos, svel, srho, sid, nullptr);
             }
