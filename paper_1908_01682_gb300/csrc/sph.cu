@@ -245,7 +245,7 @@ __device__ __forceinline__ void walk_tile(PairAcc<T, MODE> &A, const Geo<T> &G, 
 }
 
 template <class T, int DIM, int MODE>
-__global__ void __launch_bounds__(kTileThreads, sizeof(T) == 4 ? (MODE == 2 ? 4 : 3) : 1)
+__global__ void __launch_bounds__(kTileThreads, sizeof(T) == 4 ? ((MODE == 0 || MODE == 2) ? 4 : 3) : 1)
 k_pair_tile(Geo<T> G, Phys<T> Ph, TileCfg C, const V4<T> *__restrict__ pos, const V4<T> *__restrict__ vel,
             const T *__restrict__ rho, const uint32_t *__restrict__ id, const uint32_t *__restrict__ start, T mass,
             T *__restrict__ out_rho, T *pr_out, V4<T> *__restrict__ out_acc, int32_t *__restrict__ cnt,
