@@ -611,8 +611,11 @@ def run_schemes(b, args):
 
 
 def run_e2e(b, ctx, w, args, dist):
-    """Same metric through the public API with pinned host buffers: per step,
-    upload the state (tfsph_set_state), step, and read the new state back."""
+    """Same metric through the public API with page-locked host buffers: the
+    state lives on the host and every step uploads it (tfsph_set_state),
+    steps, and reads the new state back into the same buffers, so the timed
+    steps follow the same trajectory as the device-timed run (W untimed
+    steps from the initial state, then K timed ones)."""
     import numpy as np
     import torch
 
@@ -624,21 +627,22 @@ def run_e2e(b, ctx, w, args, dist):
     keep = [pinned(w.gx), pinned(w.gv), pinned(w.dx), pinned(w.du), pinned(w.tstop)]
     ge = pinned(w.ge) if w.ge is not None else None
     gx, gv, dx, du, ts = (t.numpy() for t in keep)
-    outs = {f: torch.empty((w.dim, w.n_gas if f in (b.TFSPH_FIELD_POS_G, b.TFSPH_FIELD_VEL_G) else w.n_dust),
-                           dtype=torch.float32, pin_memory=True)
-            for f in (b.TFSPH_FIELD_POS_G, b.TFSPH_FIELD_VEL_G, b.TFSPH_FIELD_POS_D, b.TFSPH_FIELD_VEL_D)}
+    outs = {b.TFSPH_FIELD_POS_G: gx, b.TFSPH_FIELD_VEL_G: gv, b.TFSPH_FIELD_POS_D: dx, b.TFSPH_FIELD_VEL_D: du}
+    if ge is not None:
+        outs[b.TFSPH_FIELD_ENERGY_G] = ge.numpy()
     h2d = 4 * (gx.size + gv.size + dx.size + du.size + ts.size + (w.n_gas if ge is not None else 0)) + \
         (w.n_gas if w.frozen is not None else 0)
-    d2h = sum(4 * t.numel() for t in outs.values())
+    d2h = sum(4 * a.size for a in outs.values())
 
     def one():
         ctx.set_state(gx, gv, dx, du, ts, ge=None if ge is None else ge.numpy(), frozen=w.frozen)
         ctx.step(w.tau, w.g)
-        for f, t in outs.items():
-            ctx.field(f, out=t.numpy())
+        for f, a in outs.items():
+            ctx.field(f, out=a)
 
-    one()
-    k = max(1, min(args.steps, 10))
+    for _ in range(max(1, args.warmup)):
+        one()
+    k = max(1, args.steps)
     dist.barrier()
     torch.cuda.synchronize()
     t0 = time.perf_counter()
