@@ -390,8 +390,12 @@ def run_ours(args, dist: Dist):
         peak = float(pk.get("hbm_gbs", 6800.0))
         unit = "GB/s"
     else:
-        mhz = clk.get("sm_mhz") or float(pk.get("clocks_under_load", {}).get("sm_mhz_median", 0) or 0) \
-            or float(pk.get("sm_max_mhz", 2070.0))
+        mhz, mhz_src = clk.get("sm_mhz"), "SM clock sampled during the timed steps"
+        if not mhz:
+            mhz = float(pk.get("clocks_under_load", {}).get("sm_mhz_median", 0) or 0)
+            mhz_src = "SM clock under load from the measured peaks file"
+        if not mhz:
+            mhz, mhz_src = float(pk.get("sm_max_mhz", 2070.0)), "maximum SM clock"
         achieved = amount / (phase_avg[dominant] * 1e-3) / 1e12
         peak = fp32_alu_peak_tflops(sm_count, mhz)
         unit = "TFLOP/s"
@@ -399,7 +403,8 @@ def run_ours(args, dist: Dist):
         + (24.0 + 32.0) * w.n_gas
     roof = {"kernel": dominant, "bound": bound, "achieved": achieved, "peak": peak, "unit": unit,
             "frac": achieved / peak, "traffic": recorded_traffic(args.workload, dominant),
-            "peak_source": f"{pk_src}" + ("" if bound == "hbm" else f" (FP32 FMA lanes x {sm_count} SMs x SM clock)"),
+            "peak_source": pk_src if bound == "hbm" else
+            f"derived: 128 FP32 FMA lanes x 2 flops x {sm_count} SMs x {mhz:.0f} MHz ({mhz_src})",
             "step_hbm_frac": (step_bytes / (ms_per_step * 1e-3) / 1e9) / float(pk.get("hbm_gbs", 6800.0)),
             "step_algorithmic_bytes": step_bytes}
 

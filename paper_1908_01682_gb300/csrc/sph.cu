@@ -172,8 +172,9 @@ __device__ __forceinline__ int floor_int(float x) { return __float2int_rd(x); }
 __device__ __forceinline__ int floor_int(double x) { return __double2int_rd(x); }
 
 // Candidate walk of one owned particle over the staged tile (REC: the
-// density pass recording the neighbour list).
-template <class T, int DIM, int MODE, bool REC>
+// density pass recording the neighbour list; SEAMLESS: no halo cell of the
+// tile lies across a periodic seam, so every row is one plain range).
+template <class T, int DIM, int MODE, bool REC, bool SEAMLESS>
 __device__ __forceinline__ void walk_tile(PairAcc<T, MODE> &A, const Geo<T> &G, const Phys<T> &Ph, const TileCfg &C,
                                           const int c0[3], const V4<T> &pa, const int *lstart, const V4<T> *spos,
                                           const V4<T> *svel, const T *srho, const uint32_t *sid, NbRec *rec)
@@ -201,7 +202,7 @@ __device__ __forceinline__ void walk_tile(PairAcc<T, MODE> &A, const Geo<T> &G, 
             const T s = slab_dist(oz, fz) * G.w[2];
             dz2 = s * s;
             if (dz2 >= G.lim2) continue;
-            seam_z = halo_seam(G, 2, c0[2], hz + oz);
+            if (!SEAMLESS) seam_z = halo_seam(G, 2, c0[2], hz + oz);
         }
 #pragma unroll 1
         for (int oy = -Ry; oy <= Ry; ++oy) {
@@ -211,7 +212,7 @@ __device__ __forceinline__ void walk_tile(PairAcc<T, MODE> &A, const Geo<T> &G, 
                 const T s = slab_dist(oy, fy) * G.w[1];
                 dy2 = s * s;
                 if (dz2 + dy2 >= G.lim2) continue;
-                seam_y = halo_seam(G, 1, c0[1], hy + oy);
+                if (!SEAMLESS) seam_y = halo_seam(G, 1, c0[1], hy + oy);
             }
             // x window: the cells whose slab lies within t = sqrt(rem)/w of the
             // particle, (o - fx) <= t for o > 0 and (fx + |o| - 1) <= t for o < 0
@@ -220,6 +221,11 @@ __device__ __forceinline__ void walk_tile(PairAcc<T, MODE> &A, const Geo<T> &G, 
             const int olo = -min(G.R[0], max(0, floor_int(t - fx + T(1))));
             const int hrow = C.H[0] * ((hy + oy) + C.H[1] * (hz + oz));
             const int u0 = hx + olo, u1 = hx + ohi + 1;  // halo x cells [u0, u1)
+            if (SEAMLESS) {
+                walk_smem_range<T, DIM, MODE, false, REC>(A, G, Ph, pa, spos, svel, srho, sid, lstart[hrow + u0],
+                                                          lstart[hrow + u1], rec);
+                continue;
+            }
             // [u0, a0) across the low seam, [a0, a1) inside, [a1, u1) across the high seam
             const int a0 = min(max(u0, sx0), u1);
             const int a1 = max(min(u1, sx1), a0);
@@ -330,6 +336,12 @@ k_pair_tile(Geo<T> G, Phys<T> Ph, TileCfg C, const V4<T> *__restrict__ pos, cons
         __syncthreads();
     }
 
+    // no halo cell across a periodic seam: the walks take the plain path
+    bool seamless = true;
+#pragma unroll
+    for (int k = 0; k < DIM; ++k)
+        if (G.per[k] && (c0[k] < G.R[k] || c0[k] + ext[k] + G.R[k] > G.n[k])) seamless = false;
+
     for (int p = tid; p < owned; p += blockDim.x) {
         // owned row of p: the last r with rowpref[r] <= p
         int lo = 0, hi = C.nrows - 1;
@@ -356,7 +368,10 @@ k_pair_tile(Geo<T> G, Phys<T> Ph, TileCfg C, const V4<T> *__restrict__ pos, cons
             if (MODE == 0 && listed) {
                 // density pass: record the neighbours in walk order
                 NbRec rec{nbl.idx + lbase, oc, nbl.cap, 0};
-                walk_tile<T, DIM, MODE, true>(A, G, Ph, C, c0, pa, lstart, spos, svel, srho, sid, &rec);
+                if (seamless)
+                    walk_tile<T, DIM, MODE, true, true>(A, G, Ph, C, c0, pa, lstart, spos, svel, srho, sid, &rec);
+                else
+                    walk_tile<T, DIM, MODE, true, false>(A, G, Ph, C, c0, pa, lstart, spos, svel, srho, sid, &rec);
                 nbl.cnt[(size_t)blockIdx.x * oc + p] = rec.n <= nbl.cap ? (uint16_t)rec.n : kNbNone;
             } else if (MODE == 2 && listed && nbl.cnt[(size_t)blockIdx.x * oc + p] != kNbNone) {
                 // force pass: the density pass's list of this binning, same order
@@ -389,8 +404,10 @@ k_pair_tile(Geo<T> G, Phys<T> Ph, TileCfg C, const V4<T> *__restrict__ pos, cons
                     for (int u = 0; u < 8; ++u) pair(ent[u]);
                 }
                 for (; q < n; ++q) pair(__ldg(&e[(size_t)q * st]));
+            } else if (seamless) {
+                walk_tile<T, DIM, MODE, false, true>(A, G, Ph, C, c0, pa, lstart, spos, svel, srho, sid, nullptr);
             } else {
-                walk_tile<T, DIM, MODE, false>(A, G, Ph, C, c0, pa, lstart, spos, svel, srho, sid, nullptr);
+                walk_tile<T, DIM, MODE, false, false>(A, G, Ph, C, c0, pa, lstart, spos, svel, srho, sid, nullptr);
             }
         }
         acc_store(A, Ph, a, mass, vel, out_rho, pr_out, out_acc, cnt, fpr);

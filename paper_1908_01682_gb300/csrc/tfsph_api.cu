@@ -918,8 +918,10 @@ int tfsph_fields(tfsph_ctx *c, int field, void *out, int mem_kind, int order)
     if (P->n == 0) return TFSPH_OK;
     if (!out) return fail(c, TFSPH_E_INVALID_ARG, "out is NULL");
     const size_t bytes = (size_t)ncomp * (size_t)P->n * c->tsize;
-    if (mem_kind == TFSPH_MEM_HOST) {
-        // a page-locked host buffer is written by the kernel directly
+    if (mem_kind == TFSPH_MEM_HOST && order == TFSPH_ORDER_CELL) {
+        // a page-locked host buffer is written by the kernel directly when the
+        // writes are in storage order; in id order they scatter over the host
+        // link, so those go through the staging buffer and one bulk copy
         if (void *m = mapped_host(out)) {
             TF_CUDA(c, launch_unpack(L, *P, what, m, order, aux));
             TF_CUDA(c, cudaStreamSynchronize(c->stream));

@@ -328,8 +328,9 @@ def test_step_adjoint_after_load_reuses_forward_quantities(orc):
 
 
 def test_page_locked_host_buffers_match_pageable(orc):
-    """set_state and fields with page-locked host buffers (read and written by
-    the kernels in place) give exactly what pageable buffers (staged) give."""
+    """set_state and fields with page-locked host buffers (read by the kernels
+    in place; cell-order fields written in place, id-order fields through the
+    staging buffer) give exactly what pageable buffers (staged) give."""
     torch = pytest.importorskip("torch")
     b = gpu_lib()
     w = workloads.column2d(nside=20, precision=0)
@@ -356,12 +357,13 @@ def test_page_locked_host_buffers_match_pageable(orc):
                       b.TFSPH_FIELD_RHO_G):
                 n = w.n_gas if f in (b.TFSPH_FIELD_POS_G, b.TFSPH_FIELD_VEL_G, b.TFSPH_FIELD_RHO_G) else w.n_dust
                 shape = (n,) if f == b.TFSPH_FIELD_RHO_G else (w.dim, n)
-                if mode == "pinned":
-                    t = torch.empty(shape, dtype=torch.float32, pin_memory=True)
-                    c.field(f, out=t.numpy())
-                    res.append(t.numpy().copy())
-                else:
-                    res.append(c.field(f))
+                for order in (b.TFSPH_ORDER_ORIGINAL, b.TFSPH_ORDER_CELL):
+                    if mode == "pinned":
+                        t = torch.empty(shape, dtype=torch.float32, pin_memory=True)
+                        c.field(f, order=order, out=t.numpy())
+                        res.append(t.numpy().copy())
+                    else:
+                        res.append(c.field(f, order=order))
             outs[mode] = res
     for a, r in zip(outs["pinned"], outs["pageable"]):
         assert np.array_equal(a, r)
