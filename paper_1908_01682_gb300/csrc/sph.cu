@@ -192,10 +192,16 @@ __device__ __forceinline__ void walk_tile(PairAcc<T, MODE> &A, const Geo<T> &G, 
     // x seam bounds in halo coordinates: cells below sx0 or from sx1 on lie across
     const int sx0 = G.per[0] ? G.R[0] - c0[0] : -1;
     const int sx1 = G.per[0] ? G.n[0] - c0[0] + G.R[0] : C.H[0] + 1;
-    const int Rz = DIM > 2 ? G.R[2] : 0;
-    const int Ry = DIM > 1 ? G.R[1] : 0;
+    // z and y offsets limited like the x window (a slightly wider range than
+    // the exact slab tests below, which still decide every row)
+    int oz0 = 0, oz1 = 0;
+    if (DIM > 2) {
+        const T tz = approx_sqrt(G.lim2) * G.inv_w[2];
+        oz1 = min(G.R[2], max(0, floor_int(fz + tz)));
+        oz0 = -min(G.R[2], max(0, floor_int(tz - fz + T(1))));
+    }
 #pragma unroll 1
-    for (int oz = -Rz; oz <= Rz; ++oz) {
+    for (int oz = oz0; oz <= oz1; ++oz) {
         T dz2 = T(0);
         int seam_z = 0;
         if (DIM > 2) {
@@ -204,8 +210,14 @@ __device__ __forceinline__ void walk_tile(PairAcc<T, MODE> &A, const Geo<T> &G, 
             if (dz2 >= G.lim2) continue;
             if (!SEAMLESS) seam_z = halo_seam(G, 2, c0[2], hz + oz);
         }
+        int oy0 = 0, oy1 = 0;
+        if (DIM > 1) {
+            const T ty = approx_sqrt(G.lim2 - dz2) * G.inv_w[1];
+            oy1 = min(G.R[1], max(0, floor_int(fy + ty)));
+            oy0 = -min(G.R[1], max(0, floor_int(ty - fy + T(1))));
+        }
 #pragma unroll 1
-        for (int oy = -Ry; oy <= Ry; ++oy) {
+        for (int oy = oy0; oy <= oy1; ++oy) {
             T dy2 = T(0);
             int seam_y = 0;
             if (DIM > 1) {
