@@ -262,6 +262,40 @@ __device__ __forceinline__ void walk_tile(PairAcc<T, MODE> &A, const Geo<T> &G, 
     }
 }
 
+// Pair sums over a particle's recorded list (entries `e[k * st]`, k < n), in
+// the recorded order (SEAMLESS: the tile recorded no seam flags).
+template <class T, int DIM, int MODE, bool SEAMLESS>
+__device__ __forceinline__ void read_list(PairAcc<T, MODE> &A, const Geo<T> &G, const Phys<T> &Ph, const V4<T> &pa,
+                                          const V4<T> *spos, const uint16_t *e, size_t st, int n)
+{
+    auto pair = [&](uint32_t cur) {
+        const V4<T> pb = spos[cur & 0x7FFFu];
+        T d[3];
+        const T r2 = (!SEAMLESS && (cur & kNbSeam)) ? pair_r2<T, DIM, true>(G, pa, pb, d)
+                                                    : pair_r2<T, DIM, false>(G, pa, pb, d);
+        A.add(G, Ph, pb, nullptr, T(1), 0u, r2, d);
+    };
+    // entries in groups of 8 independent loads through the read-only path,
+    // the next group loaded while the current one is used
+    int q = 0;
+    uint32_t ent[8], nxt[8];
+    if (n >= 8) {
+#pragma unroll
+        for (int u = 0; u < 8; ++u) nxt[u] = __ldg(&e[(size_t)u * st]);
+    }
+    for (; q + 8 <= n; q += 8) {
+#pragma unroll
+        for (int u = 0; u < 8; ++u) ent[u] = nxt[u];
+        if (q + 16 <= n) {
+#pragma unroll
+            for (int u = 0; u < 8; ++u) nxt[u] = __ldg(&e[(size_t)(q + 8 + u) * st]);
+        }
+#pragma unroll
+        for (int u = 0; u < 8; ++u) pair(ent[u]);
+    }
+    for (; q < n; ++q) pair(__ldg(&e[(size_t)q * st]));
+}
+
 template <class T, int DIM, int MODE>
 __global__ void __launch_bounds__(kTileThreads, sizeof(T) == 4 ? ((MODE == 0 || MODE == 2) ? 4 : 3) : 1)
 k_pair_tile(Geo<T> G, Phys<T> Ph, TileCfg C, const V4<T> *__restrict__ pos, const V4<T> *__restrict__ vel,
@@ -390,32 +424,10 @@ k_pair_tile(Geo<T> G, Phys<T> Ph, TileCfg C, const V4<T> *__restrict__ pos, cons
                 const int n = nbl.cnt[(size_t)blockIdx.x * oc + p];
                 const uint16_t *e = nbl.idx + lbase;
                 const size_t st = oc;
-                auto pair = [&](uint32_t cur) {
-                    const V4<T> pb = spos[cur & 0x7FFFu];
-                    T d[3];
-                    const T r2 = (cur & kNbSeam) ? pair_r2<T, DIM, true>(G, pa, pb, d)
-                                                 : pair_r2<T, DIM, false>(G, pa, pb, d);
-                    A.add(G, Ph, pb, nullptr, T(1), 0u, r2, d);
-                };
-                // entries in groups of 8 independent loads through the read-only
-                // path, the next group loaded while the current one is used
-                int q = 0;
-                uint32_t ent[8], nxt[8];
-                if (n >= 8) {
-#pragma unroll
-                    for (int u = 0; u < 8; ++u) nxt[u] = __ldg(&e[(size_t)u * st]);
-                }
-                for (; q + 8 <= n; q += 8) {
-#pragma unroll
-                    for (int u = 0; u < 8; ++u) ent[u] = nxt[u];
-                    if (q + 16 <= n) {
-#pragma unroll
-                        for (int u = 0; u < 8; ++u) nxt[u] = __ldg(&e[(size_t)(q + 8 + u) * st]);
-                    }
-#pragma unroll
-                    for (int u = 0; u < 8; ++u) pair(ent[u]);
-                }
-                for (; q < n; ++q) pair(__ldg(&e[(size_t)q * st]));
+                if (seamless)
+                    read_list<T, DIM, MODE, true>(A, G, Ph, pa, spos, e, st, n);
+                else
+                    read_list<T, DIM, MODE, false>(A, G, Ph, pa, spos, e, st, n);
             } else if (seamless) {
                 walk_tile<T, DIM, MODE, false, true>(A, G, Ph, C, c0, pa, lstart, spos, svel, srho, sid, nullptr);
             } else {
