@@ -101,11 +101,13 @@ template <class T, int MODE> struct PairAcc {
     // lambda_x in ax, ay, az
 
     // candidate b: position (with p_b/rho_b^2 in .w), velocity, density, id,
-    // squared distance r2 and displacement d = x_a - x_b
+    // squared distance r2 and displacement d = x_a - x_b (LISTED: b comes from
+    // the neighbour list, whose entries passed the same r2 < 4h^2 test)
+    template <bool LISTED = false>
     __device__ __forceinline__ void add(const Geo<T> &G, const Phys<T> &Ph, const V4<T> &pb, const V4<T> *vb,
                                         T rhob, uint32_t idb, T r2, const T d[3])
     {
-        if (!(r2 < G.h2x4)) return;
+        if (!LISTED && !(r2 < G.h2x4)) return;
         if (MODE == 4 || MODE == 5) {
             if (r2 == T(0)) return;  // zero displacement: no contribution
             const T inv_r = approx_rsqrt(r2);

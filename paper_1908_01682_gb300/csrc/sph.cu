@@ -273,7 +273,7 @@ __device__ __forceinline__ void read_list(PairAcc<T, MODE> &A, const Geo<T> &G, 
         T d[3];
         const T r2 = (!SEAMLESS && (cur & kNbSeam)) ? pair_r2<T, DIM, true>(G, pa, pb, d)
                                                     : pair_r2<T, DIM, false>(G, pa, pb, d);
-        A.add(G, Ph, pb, nullptr, T(1), 0u, r2, d);
+        A.template add<true>(G, Ph, pb, nullptr, T(1), 0u, r2, d);
     };
     // entries in groups of 8 independent loads through the read-only path,
     // the next group loaded while the current one is used
