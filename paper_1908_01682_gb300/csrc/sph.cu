@@ -131,12 +131,12 @@ __device__ __forceinline__ int halo_seam(const Geo<T> &G, int k, int c0, int hc)
 // (entries beyond cap are counted, not stored).
 struct NbRec {
     uint16_t *base;   // entry 0 of the particle
-    size_t stride;    // owned_cap
+    uint32_t stride;  // owned_cap (cap * owned_cap fits 32 bits)
     int cap;
     int n;
     __device__ __forceinline__ void push(int j, bool seam)
     {
-        if (n < cap) base[(size_t)n * stride] = (uint16_t)((uint32_t)j | (seam ? kNbSeam : 0u));
+        if (n < cap) base[(uint32_t)n * stride] = (uint16_t)((uint32_t)j | (seam ? kNbSeam : 0u));
         ++n;
     }
 };
@@ -207,12 +207,11 @@ __device__ __forceinline__ void walk_tile(PairAcc<T, MODE> &A, const Geo<T> &G, 
         if (DIM > 2) {
             const T s = slab_dist(oz, fz) * G.w[2];
             dz2 = s * s;
-            if (dz2 >= G.lim2) continue;
             if (!SEAMLESS) seam_z = halo_seam(G, 2, c0[2], hz + oz);
         }
         int oy0 = 0, oy1 = 0;
         if (DIM > 1) {
-            const T ty = approx_sqrt(G.lim2 - dz2) * G.inv_w[1];
+            const T ty = approx_sqrt(fmax(G.lim2 - dz2, T(0))) * G.inv_w[1];
             oy1 = min(G.R[1], max(0, floor_int(fy + ty)));
             oy0 = -min(G.R[1], max(0, floor_int(ty - fy + T(1))));
         }
@@ -223,12 +222,11 @@ __device__ __forceinline__ void walk_tile(PairAcc<T, MODE> &A, const Geo<T> &G, 
             if (DIM > 1) {
                 const T s = slab_dist(oy, fy) * G.w[1];
                 dy2 = s * s;
-                if (dz2 + dy2 >= G.lim2) continue;
                 if (!SEAMLESS) seam_y = halo_seam(G, 1, c0[1], hy + oy);
             }
             // x window: the cells whose slab lies within t = sqrt(rem)/w of the
             // particle, (o - fx) <= t for o > 0 and (fx + |o| - 1) <= t for o < 0
-            const T t = approx_sqrt(G.lim2 - dz2 - dy2) * G.inv_w[0];
+            const T t = approx_sqrt(fmax(G.lim2 - dz2 - dy2, T(0))) * G.inv_w[0];
             const int ohi = min(G.R[0], max(0, floor_int(fx + t)));
             const int olo = -min(G.R[0], max(0, floor_int(t - fx + T(1))));
             const int hrow = C.H[0] * ((hy + oy) + C.H[1] * (hz + oz));
@@ -413,7 +411,7 @@ k_pair_tile(Geo<T> G, Phys<T> Ph, TileCfg C, const V4<T> *__restrict__ pos, cons
             const size_t lbase = (size_t)blockIdx.x * (size_t)nbl.cap * oc + (size_t)p;
             if (MODE == 0 && listed) {
                 // density pass: record the neighbours in walk order
-                NbRec rec{nbl.idx + lbase, oc, nbl.cap, 0};
+                NbRec rec{nbl.idx + lbase, (uint32_t)oc, nbl.cap, 0};
                 if (seamless)
                     walk_tile<T, DIM, MODE, true, true>(A, G, Ph, C, c0, pa, lstart, spos, svel, srho, sid, &rec);
                 else
@@ -688,8 +686,12 @@ bool nblist_layout_t(const Geo<T> &G, int dim, int64_t n, int *cap, int *owned_c
     if (!plan_tiles(G, dim, mean, tile_bytes_per_particle<T, 0>(), 52 * 1024, C, smem) || C.cap > 0x7FFF) return false;
     double owned = mean;
     for (int k = 0; k < dim; ++k) owned *= (double)C.T[k];
-    *cap = (int)(32.0 * std::ceil(want / 32.0));
-    *owned_cap = (int)(32.0 * std::ceil((1.25 * owned + 32.0) / 32.0));
+    const double cap_d = 32.0 * std::ceil(want / 32.0);
+    const double oc_d = 32.0 * std::ceil((1.25 * owned + 32.0) / 32.0);
+    // a particle's entries lie within cap * owned_cap of its first (32-bit offsets)
+    if (cap_d * oc_d >= 2147483648.0) return false;
+    *cap = (int)cap_d;
+    *owned_cap = (int)oc_d;
     *tiles = (int64_t)C.nt[0] * C.nt[1] * C.nt[2];
     return true;
 }
