@@ -137,6 +137,18 @@ template <class T, int MODE> struct PairAcc {
                 ++cnt;
                 fp += (uint64_t)((idb & kIdMask) + 1u) * 0x9E3779B97F4A7C15ull;
             }
+        } else if (MODE == 2) {
+            // isothermal pressure term; (1/r) dW/dr without its factor fnorm,
+            // which acc_store applies once together with m_g
+            if (r2 == T(0)) return;  // self or coincident particle: zero gradient
+            const T inv_r = approx_rsqrt(r2);
+            const T q = r2 * inv_r * G.inv_h;
+            const T a = fmax(T(2) - q, T(0));
+            const T g = q < T(1) ? T(-3) + T(2.25) * q : (a * a) * (Ph.hm075 * inv_r);
+            const T s = (qa + pb.w) * g;
+            ax -= s * d[0];
+            ay -= s * d[1];
+            az -= s * d[2];
         } else {
             if (r2 == T(0)) return;  // self or coincident particle: zero gradient
             const T inv_r = approx_rsqrt(r2);
@@ -226,6 +238,13 @@ __device__ __forceinline__ void acc_store(const PairAcc<T, MODE> &A, const Phys<
             cnt[a] = A.cnt;
             fpr[a] = A.fp;
         }
+    } else if (MODE == 2) {
+        V4<T> o;
+        o.x = Ph.mfnorm * A.ax;
+        o.y = Ph.mfnorm * A.ay;
+        o.z = Ph.mfnorm * A.az;
+        o.w = T(0);
+        out_acc[a] = o;
     } else {
         V4<T> o;
         o.x = Ph.m_g * A.ax;

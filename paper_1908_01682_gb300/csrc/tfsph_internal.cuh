@@ -80,6 +80,8 @@ template <class T> struct Phys {
     T eta2;           // 0.01 h^2
     T h;
     T wnorm4;         // sigma_d / h^d / 4: the density sums accumulate 4 W / (sigma_d / h^d)
+    T mfnorm;         // m_g sigma_d / h^(d+2): the isothermal force sums accumulate (1/r) dW/dr / fnorm
+    T hm075;          // -3/4 h
     int eos;
     int av;
 };
@@ -244,6 +246,8 @@ void make_geo_phys(const tfsph_params &p, const int ncell[3], uint32_t ncells, G
     Ph.eta2 = T(0.01 * p.h * p.h);
     Ph.h = T(p.h);
     Ph.wnorm4 = T(0.25 * sigma / pow(p.h, p.dim));
+    Ph.mfnorm = T(p.m_gas * sigma / pow(p.h, p.dim + 2));
+    Ph.hm075 = T(-0.75 * p.h);
     Ph.eos = p.eos;
     Ph.av = (p.av_alpha > 0.0 || p.av_beta > 0.0) ? 1 : 0;
 }
