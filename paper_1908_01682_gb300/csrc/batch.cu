@@ -224,7 +224,7 @@ template <class T> __device__ void ph_count(const BatchArgs<T> &B)
     for (uint32_t i = thread_rank(); i < B.ng + B.nd; i += thread_count()) {
         const bool gas = i < B.ng;
         const uint32_t k = gas ? B.gkey[i] : B.dkey[i - B.ng];
-        if (k < B.ncells) atomicAdd(gas ? &B.gcnt[k] : &B.dcnt[k], 1u);
+        if (k < B.ncells) count_add_agg(gas ? &B.gcnt[k] : &B.dcnt[k]);
         else atomicOr(B.err, kErrInternal);
     }
 }
@@ -292,8 +292,8 @@ template <class T> __device__ void ph_scan_down(const BatchArgs<T> &B)
 template <class T> __device__ void ph_scatter(const BatchArgs<T> &B, int q)
 {
     for (uint32_t i = thread_rank(); i < B.ng + B.nd; i += thread_count()) {
-        if (i < B.ng) scatter_one(i, B.gkey, B.gid[q], B.gcnt, B.gstart, B.gsrc, B.gtid, B.ng, B.err);
-        else scatter_one(i - B.ng, B.dkey, B.did[q], B.dcnt, B.dstart, B.dsrc, B.dtid, B.nd, B.err);
+        if (i < B.ng) scatter_one_agg(i, B.gkey, B.gid[q], B.gcnt, B.gstart, B.gsrc, B.gtid, B.ng, B.err);
+        else scatter_one_agg(i - B.ng, B.dkey, B.did[q], B.dcnt, B.dstart, B.dsrc, B.dtid, B.nd, B.err);
     }
 }
 

@@ -13,6 +13,8 @@
 //                state is copied there (double buffer).
 // Also: packing of user arrays, field export, t_stop updates, input checks
 // and the Courant speed reduction.
+#include <algorithm>
+
 #include "sort_ops.cuh"
 
 namespace tfsph {
@@ -27,12 +29,17 @@ __global__ void k_keys(Geo<T> G, const V4<T> *__restrict__ pos, int n, uint32_t 
     key[i] = cell_key<T, DIM>(G, p.x, p.y, p.z);
 }
 
+// AGG: the warp's atomics on one counter are combined (cells holding several
+// particles of a phase).
+template <bool AGG>
 __global__ void k_count(const uint32_t *__restrict__ kg, int ng, uint32_t *__restrict__ cg,
                         const uint32_t *__restrict__ kd, int nd, uint32_t *__restrict__ cd)
 {
     const int i = blockIdx.x * blockDim.x + threadIdx.x;
-    if (i < ng) atomicAdd(&cg[kg[i]], 1u);
-    else if (i < ng + nd) atomicAdd(&cd[kd[i - ng]], 1u);
+    if (i >= ng + nd) return;
+    uint32_t *c = i < ng ? &cg[kg[i]] : &cd[kd[i - ng]];
+    if (AGG) count_add_agg(c);
+    else atomicAdd(c, 1u);
 }
 
 // Block-wide exclusive scan of one value per thread; returns the block total.
@@ -126,6 +133,7 @@ k_scan_down(const uint32_t *__restrict__ cg, const uint32_t *__restrict__ cd, ui
     if (blockIdx.x == 0 && threadIdx.x == 0) st[ncells] = blockIdx.y == 0 ? ng : nd;
 }
 
+template <bool AGG>
 __global__ void k_scatter(const uint32_t *__restrict__ kg, const uint32_t *__restrict__ idg,
                           uint32_t *__restrict__ cg, const uint32_t *__restrict__ sg, uint32_t *__restrict__ srcg,
                           uint32_t *__restrict__ tidg, int ng, const uint32_t *__restrict__ kd,
@@ -134,8 +142,13 @@ __global__ void k_scatter(const uint32_t *__restrict__ kg, const uint32_t *__res
                           uint32_t *__restrict__ tidd, int nd, int *err)
 {
     const int i = blockIdx.x * blockDim.x + threadIdx.x;
-    if (i < ng) scatter_one((uint32_t)i, kg, idg, cg, sg, srcg, tidg, (uint32_t)ng, err);
-    else if (i < ng + nd) scatter_one((uint32_t)(i - ng), kd, idd, cd, sd, srcd, tidd, (uint32_t)nd, err);
+    if (AGG) {
+        if (i < ng) scatter_one_agg((uint32_t)i, kg, idg, cg, sg, srcg, tidg, (uint32_t)ng, err);
+        else if (i < ng + nd) scatter_one_agg((uint32_t)(i - ng), kd, idd, cd, sd, srcd, tidd, (uint32_t)nd, err);
+    } else {
+        if (i < ng) scatter_one((uint32_t)i, kg, idg, cg, sg, srcg, tidg, (uint32_t)ng, err);
+        else if (i < ng + nd) scatter_one((uint32_t)(i - ng), kd, idd, cd, sd, srcd, tidd, (uint32_t)nd, err);
+    }
 }
 
 template <class T>
@@ -387,8 +400,12 @@ cudaError_t bin_t(const LaunchCtx &L, const void *geo, PhaseBufs &G, PhaseBufs &
     const int ng = (int)G.n, nd = (int)D.n;
     const int ntot = ng + nd;
     const uint32_t ncells = Gm.ncells;
-    if (ntot > 0)
-        k_count<<<grid_for(ntot, 256), 256, 0, L.stream>>>(G.key, ng, G.count, D.key, nd, D.count);
+    // combined atomics pay when a phase has on average more than one particle per cell
+    const bool agg = (double)std::max(ng, nd) >= 1.5 * (double)ncells;
+    if (ntot > 0) {
+        if (agg) k_count<true><<<grid_for(ntot, 256), 256, 0, L.stream>>>(G.key, ng, G.count, D.key, nd, D.count);
+        else k_count<false><<<grid_for(ntot, 256), 256, 0, L.stream>>>(G.key, ng, G.count, D.key, nd, D.count);
+    }
     if (L.ev) cudaEventRecord(L.ev[1], L.stream);
     dim3 sg((unsigned)nblk, 2);
     k_scan_reduce<<<sg, kScanThreads, 0, L.stream>>>(G.count, D.count, ncells, bsum, (uint32_t)nblk);
@@ -397,9 +414,10 @@ cudaError_t bin_t(const LaunchCtx &L, const void *geo, PhaseBufs &G, PhaseBufs &
                                                    D.start, (uint32_t)ng, (uint32_t)nd);
     if (L.ev) cudaEventRecord(L.ev[2], L.stream);
     if (ntot > 0) {
-        k_scatter<<<grid_for(ntot, 256), 256, 0, L.stream>>>(G.key, G.id[G.cur], G.count, G.start, G.tmp_src,
-                                                             G.tmp_id, ng, D.key, D.id[D.cur], D.count, D.start,
-                                                             D.tmp_src, D.tmp_id, nd, L.d_err);
+        auto scatter = agg ? k_scatter<true> : k_scatter<false>;
+        scatter<<<grid_for(ntot, 256), 256, 0, L.stream>>>(G.key, G.id[G.cur], G.count, G.start, G.tmp_src, G.tmp_id,
+                                                           ng, D.key, D.id[D.cur], D.count, D.start, D.tmp_src,
+                                                           D.tmp_id, nd, L.d_err);
         if (L.ev) cudaEventRecord(L.ev[3], L.stream);
         const int og = G.cur ^ 1, od = D.cur ^ 1;
         k_rank_gather<T><<<grid_for(ntot, 256), 256, 0, L.stream>>>(

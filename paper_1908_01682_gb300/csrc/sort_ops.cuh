@@ -27,6 +27,70 @@ __device__ __forceinline__ void scatter_one(uint32_t i, const uint32_t *__restri
     tid[slot] = id[i] & kIdMask;
 }
 
+// Runs of consecutive lanes of a full warp that hold the same counter take
+// it with one atomic, issued by the run's first lane. After the previous
+// sort, the particles of a cell sit next to each other in storage, so a cell
+// holding several particles of a phase costs one atomic per warp instead of
+// one per particle. Returns the run's first lane and sets *m to its length
+// and *full to whether the whole warp took part (if not, each lane is a run
+// of its own).
+__device__ __forceinline__ int counter_run(const uint32_t *c, uint32_t *m, bool *full)
+{
+    const unsigned act = __activemask();
+    const int lane = (int)(threadIdx.x & 31u);
+    *full = act == 0xffffffffu;
+    if (!*full) {
+        *m = 1u;
+        return lane;
+    }
+    const unsigned long long a = (unsigned long long)c;
+    const unsigned long long prev = __shfl_up_sync(0xffffffffu, a, 1);
+    const unsigned heads = __ballot_sync(0xffffffffu, lane == 0 || prev != a);
+    const unsigned le = lane == 31 ? 0xffffffffu : ((1u << (lane + 1)) - 1u);
+    const int first = 31 - __clz(heads & le);
+    const unsigned after = heads & ~le;
+    const int end = after ? __ffs(after) - 1 : 32;
+    *m = (uint32_t)(end - first);
+    return first;
+}
+
+__device__ __forceinline__ void count_add_agg(uint32_t *c)
+{
+    uint32_t m;
+    bool full;
+    const int first = counter_run(c, &m, &full);
+    if ((int)(threadIdx.x & 31u) == first) atomicAdd(c, m);
+}
+
+// scatter_one with the atomics of a run of lanes on one counter combined:
+// each lane receives the value a lone atomicSub of its own would have
+// returned, in lane order within the run.
+__device__ __forceinline__ void scatter_one_agg(uint32_t i, const uint32_t *__restrict__ key,
+                                                const uint32_t *__restrict__ id, uint32_t *__restrict__ cnt,
+                                                const uint32_t *__restrict__ start, uint32_t *__restrict__ src,
+                                                uint32_t *__restrict__ tid, uint32_t n, int *err)
+{
+    const uint32_t k = key[i];
+    uint32_t *c = &cnt[k];
+    uint32_t m;
+    bool full;
+    const int first = counter_run(c, &m, &full);
+    const int lane = (int)(threadIdx.x & 31u);
+    const uint32_t rank = (uint32_t)(lane - first);
+    uint32_t old = 0;
+    if (rank == 0u) old = atomicSub(c, m);
+    if (full) old = __shfl_sync(0xffffffffu, old, first);
+    const uint32_t mine = old - rank;  // this lane's share of the count
+    const uint32_t slot = start[k] + mine - 1u;
+    if (old <= rank || slot >= n) {
+        atomicAdd(c, 1u);
+        atomicOr(err, kErrInternal);
+        return;
+    }
+    src[slot] = i;
+    tid[slot] = id[i] & kIdMask;
+}
+
 template <class T>
 __device__ __forceinline__ void rank_move(uint32_t s, const uint32_t *__restrict__ key,
                                           const uint32_t *__restrict__ start, const uint32_t *__restrict__ src,
