@@ -26,7 +26,7 @@ namespace tfsph {
 namespace {
 
 template <class T, class A, int DIM>
-__global__ void __launch_bounds__(kCellsPerCta)
+__global__ void __launch_bounds__(kCellsPerCta, (sizeof(T) == 4 && sizeof(A) == 4) ? 12 : 1)
 k_cell_update(Geo<T> G, Phys<T> Ph, A tau, A g0, A g1, A g2, int harmonic, int has_frozen, int adiabatic,
               V4<T> *__restrict__ gpos, V4<T> *__restrict__ gvel, const uint32_t *__restrict__ gid,
               uint32_t *__restrict__ gkey, const uint32_t *__restrict__ gstart, const V4<T> *__restrict__ acc,

@@ -26,24 +26,35 @@ __device__ __forceinline__ int cell_drag_solve(const Phys<T> &Ph, A tau, const A
 {
     A N = A(0), L = A(0), st = A(0);
     A sv[3] = {A(0), A(0), A(0)}, sa[3] = {A(0), A(0), A(0)}, su[3] = {A(0), A(0), A(0)};
-    for (uint32_t a = gs; a < ge; ++a) {
-        if (has_frozen && (gid[a] & kFrozenBit)) continue;
-        const V4<T> v = gvel[a];
-        const V4<T> ac = acc[a];
+    auto add_gas = [&](uint32_t idv, const V4<T> &v, const V4<T> &ac) {
+        if (has_frozen && (idv & kFrozenBit)) return;
         N += A(1);
         sv[0] += A(v.x);
         sa[0] += A(ac.x);
         if (DIM > 1) { sv[1] += A(v.y); sa[1] += A(ac.y); }
         if (DIM > 2) { sv[2] += A(v.z); sa[2] += A(ac.z); }
-    }
-    for (uint32_t j = ds; j < de; ++j) {
-        const V4<T> u = dvel[j];
+    };
+    auto add_dust = [&](const V4<T> &u) {
         L += A(1);
         su[0] += A(u.x);
         if (DIM > 1) su[1] += A(u.y);
         if (DIM > 2) su[2] += A(u.z);
         st += harmonic ? A(1) / A(u.w) : A(u.w);
+    };
+    // the first gas and dust particles are loaded together (the usual cell
+    // holds one or a few of each), the rest in storage order
+    V4<T> v0{}, a0{}, u0{};
+    uint32_t id0 = 0u;
+    if (gs < ge) {
+        v0 = gvel[gs];
+        a0 = acc[gs];
+        if (has_frozen) id0 = gid[gs];
     }
+    if (ds < de) u0 = dvel[ds];
+    if (gs < ge) add_gas(id0, v0, a0);
+    for (uint32_t a = gs + 1; a < ge; ++a) add_gas(has_frozen ? gid[a] : 0u, gvel[a], acc[a]);
+    if (ds < de) add_dust(u0);
+    for (uint32_t j = ds + 1; j < de; ++j) add_dust(dvel[j]);
     if (!(N > A(0) && L > A(0))) return 0;
     const A eps = A(Ph.m_d) * L / (A(Ph.m_g) * N);
     const A tst = harmonic ? L / st : st / L;
