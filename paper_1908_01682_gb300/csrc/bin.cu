@@ -72,6 +72,24 @@ __device__ __forceinline__ uint32_t block_exclusive_scan(uint32_t v, uint32_t &e
     return total;
 }
 
+static_assert(kScanItems == 8, "the scan kernels move each thread's counts as two 16-byte words");
+
+// The kScanItems counts of cells [base, base + kScanItems) (0 past ncells),
+// as two 16-byte loads when the run is whole (base is a multiple of 8 cells).
+__device__ __forceinline__ void load_items(const uint32_t *__restrict__ cnt, uint32_t base, uint32_t ncells,
+                                           uint32_t v[kScanItems])
+{
+    if (base + kScanItems <= ncells) {
+        const uint4 *src = reinterpret_cast<const uint4 *>(cnt + base);
+        const uint4 a = src[0], b = src[1];
+        v[0] = a.x; v[1] = a.y; v[2] = a.z; v[3] = a.w;
+        v[4] = b.x; v[5] = b.y; v[6] = b.z; v[7] = b.w;
+    } else {
+#pragma unroll
+        for (int k = 0; k < kScanItems; ++k) v[k] = base + k < ncells ? cnt[base + k] : 0u;
+    }
+}
+
 // blockIdx.y selects the phase (0 gas, 1 dust).
 __global__ void __launch_bounds__(kScanThreads)
 k_scan_reduce(const uint32_t *__restrict__ cg, const uint32_t *__restrict__ cd, uint32_t ncells,
@@ -79,12 +97,11 @@ k_scan_reduce(const uint32_t *__restrict__ cg, const uint32_t *__restrict__ cd, 
 {
     const uint32_t *cnt = blockIdx.y == 0 ? cg : cd;
     const uint32_t base = blockIdx.x * kScanTile + threadIdx.x * kScanItems;
+    uint32_t v[kScanItems];
+    load_items(cnt, base, ncells, v);
     uint32_t s = 0;
 #pragma unroll
-    for (int k = 0; k < kScanItems; ++k) {
-        const uint32_t c = base + k;
-        if (c < ncells) s += cnt[c];
-    }
+    for (int k = 0; k < kScanItems; ++k) s += v[k];
     uint32_t excl;
     const uint32_t tot = block_exclusive_scan(s, excl);
     if (threadIdx.x == 0) bsum[blockIdx.y * nblk + blockIdx.x] = tot;
@@ -114,21 +131,27 @@ k_scan_down(const uint32_t *__restrict__ cg, const uint32_t *__restrict__ cd, ui
     uint32_t *st = blockIdx.y == 0 ? sg : sd;
     const uint32_t base = blockIdx.x * kScanTile + threadIdx.x * kScanItems;
     uint32_t v[kScanItems];
+    load_items(cnt, base, ncells, v);
     uint32_t s = 0;
 #pragma unroll
-    for (int k = 0; k < kScanItems; ++k) {
-        const uint32_t c = base + k;
-        v[k] = c < ncells ? cnt[c] : 0u;
-        s += v[k];
-    }
+    for (int k = 0; k < kScanItems; ++k) s += v[k];
     uint32_t excl;
     block_exclusive_scan(s, excl);
     uint32_t run = bsum[blockIdx.y * nblk + blockIdx.x] + excl;
+    uint32_t o[kScanItems];
 #pragma unroll
     for (int k = 0; k < kScanItems; ++k) {
-        const uint32_t c = base + k;
-        if (c < ncells) st[c] = run;
+        o[k] = run;
         run += v[k];
+    }
+    if (base + kScanItems <= ncells) {
+        uint4 *dst = reinterpret_cast<uint4 *>(st + base);
+        dst[0] = make_uint4(o[0], o[1], o[2], o[3]);
+        dst[1] = make_uint4(o[4], o[5], o[6], o[7]);
+    } else {
+#pragma unroll
+        for (int k = 0; k < kScanItems; ++k)
+            if (base + k < ncells) st[base + k] = o[k];
     }
     if (blockIdx.x == 0 && threadIdx.x == 0) st[ncells] = blockIdx.y == 0 ? ng : nd;
 }

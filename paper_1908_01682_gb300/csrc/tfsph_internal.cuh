@@ -119,7 +119,7 @@ constexpr uint16_t kNbSeam = 0x8000u;
 
 // Scan partials: blocks of kScanTile cells.
 constexpr int kScanThreads = 256;
-constexpr int kScanItems = 8;
+constexpr int kScanItems = 8;  // the scan kernels move them as two 16-byte words
 constexpr int kScanTile = kScanThreads * kScanItems;
 
 // Cell-update CTA: one thread per cell in phase 1.
