@@ -258,19 +258,13 @@ __device__ __forceinline__ void acc_store(const PairAcc<T, MODE> &A, const Phys<
 // ---------------------------------------------------------------------------
 // Global-memory candidate walk (fallback, and axes whose window wraps fully)
 // ---------------------------------------------------------------------------
-struct RowRanges {
-    uint32_t b0, n0;  // wrapped part below 0
-    uint32_t b1, n1;  // wrapped part above n-1
-    uint32_t b2, n2;  // main window
-    __device__ __forceinline__ uint32_t total() const { return n0 + n1 + n2; }
-    __device__ __forceinline__ uint32_t at(uint32_t i) const
-    {
-        return i < n0 ? b0 + i : (i < n0 + n1 ? b1 + (i - n0) : b2 + (i - n0 - n1));
-    }
-};
-
 // Largest offsets (ohi >= 0, olo <= 0) along x whose cell slab lies within the
 // squared radius rem of a particle at fractional position fx.
+// Compile-time flag for the range bodies of the global walk.
+template <bool S> struct SeamTag {
+    static constexpr bool value = S;
+};
+
 template <class T>
 __device__ __forceinline__ void x_window(const Geo<T> &G, T fx, T rem, int &olo, int &ohi)
 {
@@ -288,11 +282,15 @@ __device__ __forceinline__ void x_window(const Geo<T> &G, T fx, T rem, int &olo,
     }
 }
 
-// Calls f(RowRanges) once for every row of cells (fixed y, z) that may hold
-// neighbours of a particle at (px, py, pz).
+// Calls f(b, n, seam) for every contiguous storage range [b, b + n) of cells
+// that may hold neighbours of a particle at (px, py, pz): per row of cells
+// (fixed y, z), the part of its x window wrapped below 0, the part wrapped
+// above n - 1, then the main part. seam is true when the range lies across a
+// periodic seam from the particle, so its displacements need the periodic
+// image; within the particle's own image the plain difference is exact.
 template <class T, int DIM, class F>
-__device__ __forceinline__ void for_each_row(const Geo<T> &G, const uint32_t *__restrict__ start,
-                                             T px, T py, T pz, F &&f)
+__device__ __forceinline__ void for_each_range(const Geo<T> &G, const uint32_t *__restrict__ start,
+                                               T px, T py, T pz, F &&f)
 {
     T tx, ty = T(0), tz = T(0);
     const int cx = axis_cell(px, G.lo[0], G.inv_w[0], G.n[0], tx);
@@ -307,17 +305,23 @@ __device__ __forceinline__ void for_each_row(const Geo<T> &G, const uint32_t *__
     const int ylo = DIM > 1 ? (G.full[1] ? 0 : -G.R[1]) : 0;
     const int yhi = DIM > 1 ? (G.full[1] ? G.n[1] - 1 : G.R[1]) : 0;
     const int nx = G.n[0];
+    // an axis scanned in full (its window wraps) puts every range across a seam
+    bool full_seam = false;
+#pragma unroll
+    for (int k = 0; k < DIM; ++k) full_seam = full_seam || G.full[k];
 
 #pragma unroll 1
     for (int oz = zlo; oz <= zhi; ++oz) {
         int z = 0;
         T dz2 = T(0);
+        bool zseam = false;
         if (DIM > 2) {
             if (G.full[2]) {
                 z = oz;
             } else {
                 z = axis_wrap(cz + oz, G.n[2], G.per[2]);
                 if (z < 0) continue;
+                zseam = z != cz + oz;
                 const T s = slab_dist(oz, fz) * G.w[2];
                 dz2 = s * s;
                 if (dz2 >= G.lim2) continue;
@@ -327,47 +331,46 @@ __device__ __forceinline__ void for_each_row(const Geo<T> &G, const uint32_t *__
         for (int oy = ylo; oy <= yhi; ++oy) {
             int y = 0;
             T dy2 = T(0);
+            bool yseam = false;
             if (DIM > 1) {
                 if (G.full[1]) {
                     y = oy;
                 } else {
                     y = axis_wrap(cy + oy, G.n[1], G.per[1]);
                     if (y < 0) continue;
+                    yseam = y != cy + oy;
                     const T s = slab_dist(oy, fy) * G.w[1];
                     dy2 = s * s;
                     if (dz2 + dy2 >= G.lim2) continue;
                 }
             }
+            const bool row_seam = full_seam || zseam || yseam;
             const uint32_t row = (uint32_t)nx * ((uint32_t)y + (uint32_t)G.n[1] * (uint32_t)z);
-            RowRanges rr;
-            rr.n0 = rr.n1 = 0;
-            rr.b0 = rr.b1 = 0;
             if (G.full[0]) {
-                rr.b2 = start[row];
-                rr.n2 = start[row + nx] - rr.b2;
+                const uint32_t b = start[row];
+                f(b, start[row + nx] - b, row_seam);
             } else {
                 int olo, ohi;
                 x_window(G, fx, G.lim2 - dz2 - dy2, olo, ohi);
                 int x0 = cx + olo, x1 = cx + ohi;
                 if (G.per[0]) {
                     if (x0 < 0) {
-                        rr.b0 = start[row + x0 + nx];
-                        rr.n0 = start[row + nx] - rr.b0;
+                        const uint32_t b = start[row + x0 + nx];
+                        f(b, start[row + nx] - b, true);
                         x0 = 0;
                     }
                     if (x1 >= nx) {
-                        rr.b1 = start[row];
-                        rr.n1 = start[row + (x1 - nx) + 1] - rr.b1;
+                        const uint32_t b = start[row];
+                        f(b, start[row + (x1 - nx) + 1] - b, true);
                         x1 = nx - 1;
                     }
                 } else {
                     if (x0 < 0) x0 = 0;
                     if (x1 >= nx) x1 = nx - 1;
                 }
-                rr.b2 = start[row + x0];
-                rr.n2 = start[row + x1 + 1] - rr.b2;
+                const uint32_t b = start[row + x0];
+                f(b, start[row + x1 + 1] - b, row_seam);
             }
-            f(rr);
         }
     }
 }
@@ -378,13 +381,11 @@ __device__ __forceinline__ void walk_global(PairAcc<T, MODE> &A, const Geo<T> &G
                                             const V4<T> *__restrict__ vel, const T *__restrict__ rho,
                                             const uint32_t *__restrict__ id, const uint32_t *__restrict__ start)
 {
-    for_each_row<T, DIM>(G, start, pa.x, pa.y, pa.z, [&](const RowRanges &rr) {
-        const uint32_t tot = rr.total();
-        for (uint32_t i = 0; i < tot; ++i) {
-            const uint32_t b = rr.at(i);
+    auto range = [&](uint32_t b0, uint32_t n, auto seam) {
+        for (uint32_t b = b0; b < b0 + n; ++b) {
             const V4<T> pb = pos[b];
             T d[3];
-            const T r2 = pair_r2<T, DIM, true>(G, pa, pb, d);
+            const T r2 = pair_r2<T, DIM, decltype(seam)::value>(G, pa, pb, d);
             V4<T> vb;
             T rhob = T(1);
             if (r2 < G.h2x4) {
@@ -393,6 +394,10 @@ __device__ __forceinline__ void walk_global(PairAcc<T, MODE> &A, const Geo<T> &G
             }
             A.add(G, Ph, pb, &vb, rhob, MODE == 1 ? id[b] : 0u, r2, d);
         }
+    };
+    for_each_range<T, DIM>(G, start, pa.x, pa.y, pa.z, [&](uint32_t b0, uint32_t n, bool seam) {
+        if (seam) range(b0, n, SeamTag<true>{});
+        else range(b0, n, SeamTag<false>{});
     });
 }
 

@@ -65,13 +65,11 @@ __global__ void __launch_bounds__(kXThreads) k_xsum(Geo<T> G, Phys<T> Ph, XArgs<
     T s0 = T(0), s1 = T(0);                         // rho, K (ISPH gas) / rho, e (ISPH dust)
     T a[3] = {T(0), T(0), T(0)};                    // u_a, v_j or the MK sum
     T gs[3] = {T(0), T(0), T(0)}, qs[3] = {T(0), T(0), T(0)};
-    for_each_row<T, DIM>(G, X.sstart, pt.x, pt.y, pt.z, [&](const RowRanges &rr) {
-        const uint32_t tot = rr.total();
-        for (uint32_t i = 0; i < tot; ++i) {
-            const uint32_t b = rr.at(i);
+    auto range = [&](uint32_t b0, uint32_t n, auto seam) {
+        for (uint32_t b = b0; b < b0 + n; ++b) {
             const V4<T> pb = X.spos[b];
             T d[3];
-            const T r2 = pair_r2<T, DIM, true>(G, pt, pb, d);
+            const T r2 = pair_r2<T, DIM, decltype(seam)::value>(G, pt, pb, d);
             if (!(r2 < G.h2x4)) continue;
             const V4<T> vb = X.svel[b];
             const T r = approx_sqrt(r2);
@@ -79,14 +77,14 @@ __global__ void __launch_bounds__(kXThreads) k_xsum(Geo<T> G, Phys<T> Ph, XArgs<
             if (KIND == kIsphAtGas) {
                 const T w = Ph.m_d * W;
                 s0 += w;
-                s1 += w / vb.w;  // t_j
-                const T c = w / X.srho[b];
+                s1 += approx_div(w, vb.w);  // t_j
+                const T c = approx_div(w, X.srho[b]);
                 a[0] += c * vb.x;
                 a[1] += c * vb.y;
                 a[2] += c * vb.z;
             } else if (KIND == kIsphAtDust) {
                 const T w = Ph.m_g * W;
-                const T inv_rho = T(1) / X.srho[b];
+                const T inv_rho = approx_div(T(1), X.srho[b]);
                 s0 += w;
                 if (Ph.eos == TFSPH_EOS_ADIABATIC) s1 += w * vb.w * inv_rho;
                 if (!(X.has_frozen && (X.sid[b] & kFrozenBit))) {
@@ -95,7 +93,7 @@ __global__ void __launch_bounds__(kXThreads) k_xsum(Geo<T> G, Phys<T> Ph, XArgs<
                     a[2] += w * vb.z * inv_rho;
                 }
                 if (r2 > T(0)) {
-                    const T F = Ph.m_g * kernel_f(G, r * G.inv_h, G.h / r);  // m_g (1/r) dW/dr
+                    const T F = Ph.m_g * kernel_f(G, r * G.inv_h, approx_div(G.h, r));  // m_g (1/r) dW/dr
                     const T q = pb.w;                                       // p_a / rho_a^2
                     for (int k = 0; k < 3; ++k) {
                         gs[k] += F * d[k];
@@ -108,13 +106,17 @@ __global__ void __launch_bounds__(kXThreads) k_xsum(Geo<T> G, Phys<T> Ph, XArgs<
                 T rel;
                 if (KIND == kMkAtGas) rel = (vt.x - vb.x) * d[0] + (vt.y - vb.y) * d[1] + (vt.z - vb.z) * d[2];
                 else rel = (vb.x - vt.x) * d[0] + (vb.y - vt.y) * d[1] + (vb.z - vt.z) * d[2];
-                const T coef = KIND == kMkAtGas ? T(1) / vb.w : T(1) / X.srho[b];
-                const T f = coef * rel / (r2 + eta2) * W;
+                const T coef = approx_div(T(1), KIND == kMkAtGas ? vb.w : X.srho[b]);
+                const T f = approx_div(coef * rel, r2 + eta2) * W;
                 a[0] += f * d[0];
                 a[1] += f * d[1];
                 a[2] += f * d[2];
             }
         }
+    };
+    for_each_range<T, DIM>(G, X.sstart, pt.x, pt.y, pt.z, [&](uint32_t b0, uint32_t n, bool seam) {
+        if (seam) range(b0, n, SeamTag<true>{});
+        else range(b0, n, SeamTag<false>{});
     });
     V4<T> o;
     if (KIND == kIsphAtGas) {
