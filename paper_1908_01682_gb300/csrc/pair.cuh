@@ -258,28 +258,25 @@ __device__ __forceinline__ void acc_store(const PairAcc<T, MODE> &A, const Phys<
 // ---------------------------------------------------------------------------
 // Global-memory candidate walk (fallback, and axes whose window wraps fully)
 // ---------------------------------------------------------------------------
-// Largest offsets (ohi >= 0, olo <= 0) along x whose cell slab lies within the
-// squared radius rem of a particle at fractional position fx.
 // Compile-time flag for the range bodies of the global walk.
 template <bool S> struct SeamTag {
     static constexpr bool value = S;
 };
 
+// floor(x) as an int, in one conversion (x is a small cell offset).
+__device__ __forceinline__ int floor_int(float x) { return __float2int_rd(x); }
+__device__ __forceinline__ int floor_int(double x) { return __double2int_rd(x); }
+
+// Offsets (ohi >= 0, olo <= 0) along x of the cells whose slab lies within
+// the squared radius rem of a particle at fractional position fx (the
+// closed form of the tile walk's x window; at most one cell wider than the
+// exact slab test at its ends).
 template <class T>
 __device__ __forceinline__ void x_window(const Geo<T> &G, T fx, T rem, int &olo, int &ohi)
 {
-    ohi = 0;
-    olo = 0;
-#pragma unroll 1
-    for (int o = 1; o <= G.R[0]; ++o) {
-        const T s = slab_dist(o, fx) * G.w[0];
-        if (s * s < rem) ohi = o; else break;
-    }
-#pragma unroll 1
-    for (int o = 1; o <= G.R[0]; ++o) {
-        const T s = slab_dist(-o, fx) * G.w[0];
-        if (s * s < rem) olo = -o; else break;
-    }
+    const T t = approx_sqrt(fmax(rem, T(0))) * G.inv_w[0];
+    ohi = min(G.R[0], max(0, floor_int(fx + t)));
+    olo = -min(G.R[0], max(0, floor_int(t - fx + T(1))));
 }
 
 // Calls f(b, n, seam) for every contiguous storage range [b, b + n) of cells
@@ -300,10 +297,18 @@ __device__ __forceinline__ void for_each_range(const Geo<T> &G, const uint32_t *
     const T fy = DIM > 1 ? ty - T(cy) : T(0);
     const T fz = DIM > 2 ? tz - T(cz) : T(0);
 
-    const int zlo = DIM > 2 ? (G.full[2] ? 0 : -G.R[2]) : 0;
-    const int zhi = DIM > 2 ? (G.full[2] ? G.n[2] - 1 : G.R[2]) : 0;
-    const int ylo = DIM > 1 ? (G.full[1] ? 0 : -G.R[1]) : 0;
-    const int yhi = DIM > 1 ? (G.full[1] ? G.n[1] - 1 : G.R[1]) : 0;
+    // offsets bounded like the x window (the slab tests below still decide
+    // every row); an axis whose window wraps is scanned in full
+    int zlo = 0, zhi = 0;
+    if (DIM > 2) {
+        if (G.full[2]) {
+            zhi = G.n[2] - 1;
+        } else {
+            const T t = approx_sqrt(G.lim2) * G.inv_w[2];
+            zhi = min(G.R[2], max(0, floor_int(fz + t)));
+            zlo = -min(G.R[2], max(0, floor_int(t - fz + T(1))));
+        }
+    }
     const int nx = G.n[0];
     // an axis scanned in full (its window wraps) puts every range across a seam
     bool full_seam = false;
@@ -325,6 +330,16 @@ __device__ __forceinline__ void for_each_range(const Geo<T> &G, const uint32_t *
                 const T s = slab_dist(oz, fz) * G.w[2];
                 dz2 = s * s;
                 if (dz2 >= G.lim2) continue;
+            }
+        }
+        int ylo = 0, yhi = 0;
+        if (DIM > 1) {
+            if (G.full[1]) {
+                yhi = G.n[1] - 1;
+            } else {
+                const T t = approx_sqrt(G.lim2 - dz2) * G.inv_w[1];
+                yhi = min(G.R[1], max(0, floor_int(fy + t)));
+                ylo = -min(G.R[1], max(0, floor_int(t - fy + T(1))));
             }
         }
 #pragma unroll 1

@@ -167,9 +167,6 @@ __device__ __forceinline__ void walk_smem_range(PairAcc<T, MODE> &A, const Geo<T
     }
 }
 
-// floor(x) as an int, in one conversion (x is a small cell offset).
-__device__ __forceinline__ int floor_int(float x) { return __float2int_rd(x); }
-__device__ __forceinline__ int floor_int(double x) { return __double2int_rd(x); }
 
 // Candidate walk of one owned particle over the staged tile (REC: the
 // density pass recording the neighbour list; SEAMLESS: no halo cell of the
