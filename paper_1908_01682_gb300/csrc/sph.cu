@@ -257,6 +257,24 @@ __device__ __forceinline__ void walk_tile(PairAcc<T, MODE> &A, const Geo<T> &G, 
     }
 }
 
+// One particle's sums by the global-memory walk, for tiles whose halo does
+// not fit shared memory. Kept out of line so that the rare path does not
+// weigh on the register allocation of the tiled walks.
+template <class T, int DIM, int MODE>
+__device__ __noinline__ void particle_global(const Geo<T> G, const Phys<T> Ph, uint32_t a,
+                                             const V4<T> *__restrict__ pos, const V4<T> *__restrict__ vel,
+                                             const T *__restrict__ rho, const uint32_t *__restrict__ id,
+                                             const uint32_t *__restrict__ start, T mass, T *__restrict__ out_rho,
+                                             T *pr_out, V4<T> *__restrict__ out_acc, int32_t *__restrict__ cnt,
+                                             uint64_t *__restrict__ fpr)
+{
+    PairAcc<T, MODE> A;
+    const V4<T> pa = pos[a];
+    acc_init(A, Ph, pa, vel, rho, a);
+    walk_global<T, DIM, MODE>(A, G, Ph, pa, pos, vel, rho, id, start);
+    acc_store(A, Ph, a, mass, vel, out_rho, pr_out, out_acc, cnt, fpr);
+}
+
 // Pair sums over a particle's recorded list (entries `e[k * st]`, k < n), in
 // the recorded order (SEAMLESS: the tile recorded no seam flags).
 template <class T, int DIM, int MODE, bool SEAMLESS>
@@ -392,12 +410,13 @@ k_pair_tile(Geo<T> G, Phys<T> Ph, TileCfg C, const V4<T> *__restrict__ pos, cons
         }
         const int k = p - rowpref[lo];
         const uint32_t a = (uint32_t)(rowg[lo] + k);
-        PairAcc<T, MODE> A;
         if (!tiled) {
-            const V4<T> pa = pos[a];
-            acc_init(A, Ph, pa, vel, rho, a);
-            walk_global<T, DIM, MODE>(A, G, Ph, pa, pos, vel, rho, id, start);
-        } else {
+            particle_global<T, DIM, MODE>(G, Ph, a, pos, vel, rho, id, start, mass, out_rho, pr_out, out_acc, cnt,
+                                          fpr);
+            continue;
+        }
+        PairAcc<T, MODE> A;
+        {
             // the owned row starts at halo x = R of halo row (oy + R, oz + R)
             const int oy = lo % C.T[1], oz = lo / C.T[1];
             const int hrow = C.H[0] * ((oy + (DIM > 1 ? G.R[1] : 0)) + C.H[1] * (oz + (DIM > 2 ? G.R[2] : 0)));
