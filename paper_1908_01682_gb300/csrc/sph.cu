@@ -275,6 +275,25 @@ __device__ __noinline__ void particle_global(const Geo<T> G, const Phys<T> Ph, u
     acc_store(A, Ph, a, mass, vel, out_rho, pr_out, out_acc, cnt, fpr);
 }
 
+// One particle's sums by the tile walk without recording, for the listing
+// passes (density MODE 0, isothermal force MODE 2) when the list does not
+// cover the particle; out of line for the same reason as particle_global.
+// (The density pass calls it; the force pass keeps its walk inline, where
+// the call's register saves cost more than they free.)
+template <class T, int DIM, int MODE, bool SEAMLESS>
+__device__ __noinline__ void particle_tile(const Geo<T> G, const Phys<T> Ph, const TileCfg C, int c0x, int c0y,
+                                           int c0z, const V4<T> pa, uint32_t a, const int *lstart,
+                                           const V4<T> *spos, const V4<T> *__restrict__ vel, T mass,
+                                           T *__restrict__ out_rho, T *pr_out, V4<T> *__restrict__ out_acc)
+{
+    static_assert(MODE == 0 || MODE == 2, "listing passes only");
+    PairAcc<T, MODE> A;
+    acc_init(A, Ph, pa, vel, static_cast<const T *>(nullptr), a);
+    const int c0[3] = {c0x, c0y, c0z};
+    walk_tile<T, DIM, MODE, false, SEAMLESS>(A, G, Ph, C, c0, pa, lstart, spos, nullptr, nullptr, nullptr, nullptr);
+    acc_store(A, Ph, a, mass, vel, out_rho, pr_out, out_acc, nullptr, nullptr);
+}
+
 // Pair sums over a particle's recorded list (entries `e[k * st]`, k < n), in
 // the recorded order (SEAMLESS: the tile recorded no seam flags).
 template <class T, int DIM, int MODE, bool SEAMLESS>
@@ -442,6 +461,17 @@ k_pair_tile(Geo<T> G, Phys<T> Ph, TileCfg C, const V4<T> *__restrict__ pos, cons
                     read_list<T, DIM, MODE, true>(A, G, Ph, pa, spos, e, st, n);
                 else
                     read_list<T, DIM, MODE, false>(A, G, Ph, pa, spos, e, st, n);
+            } else if (MODE == 0) {
+                // a particle the density pass does not list (rare): out of line
+                if constexpr (MODE == 0) {
+                    if (seamless)
+                        particle_tile<T, DIM, MODE, true>(G, Ph, C, c0[0], c0[1], c0[2], pa, a, lstart, spos, vel,
+                                                          mass, out_rho, pr_out, out_acc);
+                    else
+                        particle_tile<T, DIM, MODE, false>(G, Ph, C, c0[0], c0[1], c0[2], pa, a, lstart, spos, vel,
+                                                           mass, out_rho, pr_out, out_acc);
+                }
+                continue;
             } else if (seamless) {
                 walk_tile<T, DIM, MODE, false, true>(A, G, Ph, C, c0, pa, lstart, spos, svel, srho, sid, nullptr);
             } else {
