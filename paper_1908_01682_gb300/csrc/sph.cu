@@ -127,16 +127,17 @@ __device__ __forceinline__ int halo_seam(const Geo<T> &G, int k, int c0, int hc)
     return G.per[k] && (g < 0 || g >= G.n[k]);
 }
 
-// Appends the neighbours the density walk finds to the particle's list
-// (entries beyond cap are counted, not stored).
+// Appends the neighbours the density walk finds to the particle's list.
+// Entries beyond cap are counted, and written to the tile's spare row cap
+// (never read), which keeps the store unconditional.
 struct NbRec {
     uint16_t *base;   // entry 0 of the particle
-    uint32_t stride;  // owned_cap (cap * owned_cap fits 32 bits)
+    uint32_t stride;  // owned_cap ((cap + 1) * owned_cap fits 32 bits)
     int cap;
     int n;
     __device__ __forceinline__ void push(int j, bool seam)
     {
-        if (n < cap) base[(uint32_t)n * stride] = (uint16_t)((uint32_t)j | (seam ? kNbSeam : 0u));
+        base[(uint32_t)min(n, cap) * stride] = (uint16_t)((uint32_t)j | (seam ? kNbSeam : 0u));
         ++n;
     }
 };
@@ -443,7 +444,7 @@ k_pair_tile(Geo<T> G, Phys<T> Ph, TileCfg C, const V4<T> *__restrict__ pos, cons
             acc_init(A, Ph, pa, vel, rho, a);
             const bool listed = nbl.idx && p < nbl.owned_cap;
             const size_t oc = (size_t)nbl.owned_cap;
-            const size_t lbase = (size_t)blockIdx.x * (size_t)nbl.cap * oc + (size_t)p;
+            const size_t lbase = (size_t)blockIdx.x * (size_t)(nbl.cap + 1) * oc + (size_t)p;
             if (MODE == 0 && listed) {
                 // density pass: record the neighbours in walk order
                 NbRec rec{nbl.idx + lbase, (uint32_t)oc, nbl.cap, 0};
@@ -735,7 +736,7 @@ bool nblist_layout_t(const Geo<T> &G, int dim, int64_t n, int *cap, int *owned_c
     const double cap_d = 32.0 * std::ceil(want / 32.0);
     const double oc_d = 32.0 * std::ceil((1.25 * owned + 32.0) / 32.0);
     // a particle's entries lie within cap * owned_cap of its first (32-bit offsets)
-    if (cap_d * oc_d >= 2147483648.0) return false;
+    if ((cap_d + 1.0) * oc_d >= 2147483648.0) return false;
     *cap = (int)cap_d;
     *owned_cap = (int)oc_d;
     *tiles = (int64_t)C.nt[0] * C.nt[1] * C.nt[2];

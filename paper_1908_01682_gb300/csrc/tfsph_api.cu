@@ -431,7 +431,8 @@ int tfsph_init(tfsph_ctx **out, const tfsph_params *p, const void *const *gas, i
         int cap = 0, oc = 0;
         int64_t tiles = 0;
         if (nblist_layout(c->geo, c->precision, c->dim, n_gas, &cap, &oc, &tiles)) {
-            const size_t bytes = (size_t)tiles * (size_t)cap * (size_t)oc * 2;
+            // cap rows per tile plus one spare row for entries beyond cap
+            const size_t bytes = (size_t)tiles * (size_t)(cap + 1) * (size_t)oc * 2;
             if (bytes <= ((size_t)16 << 30)) {
                 void *tmp0 = nullptr;
                 if ((rc = dalloc(c, &tmp0, bytes))) return bail(rc);

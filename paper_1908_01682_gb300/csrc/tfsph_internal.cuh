@@ -103,9 +103,10 @@ struct PhaseBufs {
 // pass and read by the tiled force pass of the same binning (both passes use
 // the same tiles and visit the owned particles of a tile in the same order).
 // For owned particle p < owned_cap of tile t, entry k is
-// idx[(t * cap + k) * owned_cap + p]: the tile-local (shared-memory) index of
-// its k-th neighbour in walk order, bit 15 set for a pair across a periodic
-// seam, so a warp's accesses are contiguous. cnt[t * owned_cap + p] is the
+// idx[(t * (cap + 1) + k) * owned_cap + p]: the tile-local (shared-memory)
+// index of its k-th neighbour in walk order, bit 15 set for a pair across a
+// periodic seam, so a warp's accesses are contiguous; row cap of each tile is
+// a spare that takes (and drops) the entries beyond cap. cnt[t * owned_cap + p] is the
 // number of entries, or kNbNone when the particle has more than cap
 // neighbours; such particles (and p >= owned_cap) walk their candidates again.
 struct NbList {
