@@ -125,6 +125,17 @@ def test_all_particles_in_one_cell(orc):
     _compare(orc, w, tol=2e-5)
 
 
+def test_tile_overflowing_shared_memory(orc):
+    """A cluster of 3000 gas particles in one cell of a 16^3 box: the tiles
+    whose halo holds it do not fit shared memory and take the global-memory
+    walk (density, force and the neighbour statistics)."""
+    rng = np.random.default_rng(23)
+    w = workloads.box3d(nside=16, precision=0)
+    w.gx[:, :3000] = 0.5 + rng.uniform(0, 0.01, (3, 3000))
+    w.gx = w.gx.astype(np.float32).astype(np.float64)
+    _compare(orc, w, tol=2e-5)
+
+
 def test_particles_on_cell_faces(orc):
     """Positions exactly on cell faces and on the periodic boundary."""
     w = workloads.box3d(nside=8, precision=0)
