@@ -225,13 +225,19 @@ PHASE_SOURCE = {"count": _BIN, "scan": _BIN, "scatter": _BIN, "gather": _BIN,
 
 
 def kernel_source_hash(phase: str) -> str:
-    """sha256 of the phase's kernel sources and the shared internal header."""
+    """sha256 of the phase's kernel sources and the shared internal header,
+    without comments and blank space: an edit of the comments alone leaves
+    the recorded counters valid, any change of the code does not."""
     import hashlib
+    import re
     csrc = os.path.join(ROOT, "paper_1908_01682_gb300", "csrc")
     hsh = hashlib.sha256()
     for f in PHASE_SOURCE[phase] + ("tfsph_internal.cuh",):
-        with open(os.path.join(csrc, f), "rb") as fh:
-            hsh.update(fh.read())
+        with open(os.path.join(csrc, f), encoding="utf-8") as fh:
+            src = fh.read()
+        src = re.sub(r"/\*.*?\*/", " ", src, flags=re.S)
+        src = re.sub(r"//[^\n]*", " ", src)
+        hsh.update(" ".join(src.split()).encode())
     return hsh.hexdigest()
 
 

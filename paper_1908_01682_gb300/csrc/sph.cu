@@ -168,7 +168,6 @@ __device__ __forceinline__ void walk_smem_range(PairAcc<T, MODE> &A, const Geo<T
     }
 }
 
-
 // Candidate walk of one owned particle over the staged tile (REC: the
 // density pass recording the neighbour list; SEAMLESS: no halo cell of the
 // tile lies across a periodic seam, so every row is one plain range).
@@ -190,8 +189,9 @@ __device__ __forceinline__ void walk_tile(PairAcc<T, MODE> &A, const Geo<T> &G, 
     // x seam bounds in halo coordinates: cells below sx0 or from sx1 on lie across
     const int sx0 = G.per[0] ? G.R[0] - c0[0] : -1;
     const int sx1 = G.per[0] ? G.n[0] - c0[0] + G.R[0] : C.H[0] + 1;
-    // z and y offsets limited like the x window (a slightly wider range than
-    // the exact slab tests below, which still decide every row)
+    // z and y offsets limited by the closed form of the x window; a row may
+    // come out one cell wider than an exact slab test, which only adds
+    // candidates (each pair is decided by its own r^2 < 4h^2)
     int oz0 = 0, oz1 = 0;
     if (DIM > 2) {
         const T tz = approx_sqrt(G.lim2) * G.inv_w[2];
