@@ -264,6 +264,13 @@ def test_box3d_full_size_one_step(orc):
     _compare(orc, workloads.box3d(nside=128, precision=0))
 
 
+def test_box3d_192_one_step(orc):
+    """3D box at 3.4x the benchmark's size, 192^3 gas + 192^3 dust (14.2M
+    particles, 7.1M cells, 32,768 tiles): every output against the oracle, so
+    the index and offset arithmetic is checked beyond the benchmark's range."""
+    _compare(orc, workloads.box3d(nside=192, precision=0))
+
+
 def test_dustyshock_full_size_one_step(orc):
     _compare(orc, workloads.dustyshock(precision=0))
 
