@@ -452,7 +452,7 @@ template <int DIM, int MODE> __global__ void __launch_bounds__(kMaxBlock) k_b_pa
     ph_pair<Tf, DIM, MODE>(B, ld_parity(B.sp), si);
 }
 
-template <class A, int DIM> __global__ void __launch_bounds__(kMaxBlock) k_b_update(BatchArgs<Tf> B)
+template <class A, int DIM> __global__ void __launch_bounds__(kMaxBlock, sizeof(A) == 4 ? 3 : 1) k_b_update(BatchArgs<Tf> B)
 {
     extern __shared__ __align__(16) unsigned char smem[];
     __shared__ BInst<Tf> si;
