@@ -53,7 +53,7 @@ template <class T> struct XArgs {
 };
 
 template <class T, int DIM, int KIND>
-__global__ void __launch_bounds__(kXThreads) k_xsum(Geo<T> G, Phys<T> Ph, XArgs<T> X)
+__global__ void __launch_bounds__(kXThreads, sizeof(T) == 4 ? 12 : 1) k_xsum(Geo<T> G, Phys<T> Ph, XArgs<T> X)
 {
     const int t = blockIdx.x * blockDim.x + threadIdx.x;
     if (t >= X.n) return;
