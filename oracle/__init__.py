@@ -38,7 +38,7 @@ def build(force: bool = False) -> str:
 
 class _Params(C.Structure):
     _fields_ = [
-        ("dim", C.c_int32), ("decide_fp32", C.c_int32), ("eos", C.c_int32),
+        ("dim", C.c_int32), ("path_fp32", C.c_int32), ("eos", C.c_int32),
         ("tstar_mode", C.c_int32), ("periodic", C.c_int32 * 3), ("brute", C.c_int32),
         ("lo", C.c_double * 3), ("hi", C.c_double * 3),
         ("h", C.c_double), ("cell_size", C.c_double),
@@ -51,7 +51,7 @@ class _Params(C.Structure):
 class _StepOut(C.Structure):
     _fields_ = [
         ("rho_g", C.c_void_p), ("acc_g", C.c_void_p), ("dedt_g", C.c_void_p), ("acc_scale_g", C.c_void_p),
-        ("nb_count", C.c_void_p), ("nb_fprint", C.c_void_p),
+        ("nb_count", C.c_void_p), ("nb_fprint", C.c_void_p), ("nb_band", C.c_void_p), ("nb_band_ids", C.c_void_p),
         ("keys_g", C.c_void_p), ("keys_d", C.c_void_p),
         ("perm_g", C.c_void_p), ("perm_d", C.c_void_p),
         ("cstart_g", C.c_void_p), ("cstart_d", C.c_void_p),
@@ -79,8 +79,15 @@ def _load():
         _lib.orc_dWdr.argtypes = [C.c_int, d, d]
         _lib.orc_ncell.argtypes = [vp, vp]
         _lib.orc_bin.argtypes = [vp, i64, vp, vp, vp, vp]
-        _lib.orc_density.argtypes = [vp, i64, vp, d, vp, vp, vp]
+        _lib.orc_density.argtypes = [vp, i64, vp, d, vp, vp, vp, vp, vp]
         _lib.orc_accel.argtypes = [vp, i64, vp, vp, vp, vp, vp, vp, vp]
+        _lib.orc_neighbour.restype = C.c_int
+        _lib.orc_neighbour.argtypes = [vp, vp, vp, vp]
+        _lib.orc_cell_index.restype = i64
+        _lib.orc_cell_index.argtypes = [vp, C.c_int, d]
+        _lib.orc_dust_profile.argtypes = [vp, vp, i64, vp, d, vp]
+        _lib.orc_set_threads.restype = C.c_int
+        _lib.orc_set_threads.argtypes = [C.c_int]
         _lib.orc_max_dt.restype = d
         _lib.orc_max_dt.argtypes = [vp, i64, vp, vp, vp, d]
         _lib.orc_step.argtypes = [vp, i64, i64, vp, vp, vp, vp, vp, vp, vp, d, vp, vp, vp]
@@ -105,12 +112,12 @@ class Params:
     av_alpha: float = 0.0
     av_beta: float = 0.0
     tstar_mode: int = 0     # 0 arithmetic mean, 1 harmonic mean
-    decide_fp32: int = 0    # integer decisions in binary32 (FP32 path)
+    path_fp32: int = 0      # the path under test computes in binary32: width of the reported pair band
     brute: int = 0          # all-pairs neighbour search
 
     def c(self) -> _Params:
         p = _Params()
-        p.dim, p.decide_fp32, p.eos, p.tstar_mode = self.dim, self.decide_fp32, self.eos, self.tstar_mode
+        p.dim, p.path_fp32, p.eos, p.tstar_mode = self.dim, self.path_fp32, self.eos, self.tstar_mode
         p.brute = self.brute
         for k in range(3):
             p.periodic[k] = int(self.periodic[k]) if k < len(self.periodic) else 0
@@ -159,16 +166,44 @@ def bin_particles(p: Params, x):
     return keys, perm, cstart
 
 
-def density(p: Params, x, m: float):
-    """Summation density, neighbour counts and neighbour-set fingerprints."""
+def neighbour(p: Params, xa, xb):
+    """(inside, band) for one pair: inside = r^2 < 4h^2 over the reals; band =
+    the pair lies within 8 ulp of 4h^2 in the path's precision (or its
+    decision could not be certified)."""
+    a = _f64(list(xa) + [0.0] * (3 - len(xa)))
+    b = _f64(list(xb) + [0.0] * (3 - len(xb)))
+    band = C.c_int32(0)
+    pc = p.c()
+    inside = _load().orc_neighbour(C.byref(pc), _ptr(a), _ptr(b), C.byref(band))
+    return bool(inside), bool(band.value)
+
+
+def cell_index(p: Params, axis: int, x: float) -> int:
+    """floor((x - lo) n / L) along one axis, exact, clamped to [0, n-1]."""
+    pc = p.c()
+    return int(_load().orc_cell_index(C.byref(pc), int(axis), float(x)))
+
+
+NBAND = 4  # band partner ids reported per particle (ORC_NBAND)
+
+
+def density(p: Params, x, m: float, with_band: bool = False):
+    """Summation density, neighbour counts and neighbour-set fingerprints.
+
+    Membership is exact (r^2 < 4h^2 over the reals). Counts and fingerprints
+    cover the neighbours outside the reported band (pairs within 8 ulp of 4h^2
+    in the path's precision); with_band also returns the number of band pairs
+    per particle and the ids of the first NBAND of them (-1 beyond)."""
     x = _f64(x, (p.dim, -1))
     n = x.shape[1]
     rho = np.zeros(n)
     cnt = np.zeros(n, np.int64)
     fp = np.zeros(n, np.uint64)
+    nb = np.zeros(n, np.int64)
+    ids = np.full((n, NBAND), -1, np.int64)
     pc = p.c()
-    _load().orc_density(C.byref(pc), n, _ptr(x), m, _ptr(rho), _ptr(cnt), _ptr(fp))
-    return rho, cnt, fp
+    _load().orc_density(C.byref(pc), n, _ptr(x), m, _ptr(rho), _ptr(cnt), _ptr(fp), _ptr(nb), _ptr(ids))
+    return (rho, cnt, fp, nb, ids) if with_band else (rho, cnt, fp)
 
 
 def accel(p: Params, x, v, e, rho, with_scale: bool = False):
@@ -222,6 +257,8 @@ class StepResult:
     acc_scale_g: np.ndarray
     nb_count: np.ndarray
     nb_fprint: np.ndarray
+    nb_band: np.ndarray
+    nb_band_ids: np.ndarray
     keys_g: np.ndarray
     keys_d: np.ndarray
     perm_g: np.ndarray
@@ -251,11 +288,12 @@ def step(p: Params, s: State, tau: float, g=(0.0, 0.0, 0.0), acc_override=None) 
     nc = ncell(p)
     ncells = int(np.prod(nc))
     r = StepResult(np.zeros(ng), np.zeros((p.dim, ng)), np.zeros(ng), np.zeros(ng), np.zeros(ng, np.int64),
-                   np.zeros(ng, np.uint64), np.zeros(ng, np.int64), np.zeros(nd, np.int64),
+                   np.zeros(ng, np.uint64), np.zeros(ng, np.int64), np.full((ng, NBAND), -1, np.int64),
+                   np.zeros(ng, np.int64), np.zeros(nd, np.int64),
                    np.zeros(ng, np.int64), np.zeros(nd, np.int64),
                    np.zeros(ncells + 1, np.int64), np.zeros(ncells + 1, np.int64), 0)
     out = _StepOut(_ptr(r.rho_g), _ptr(r.acc_g), _ptr(r.dedt_g), _ptr(r.acc_scale_g), _ptr(r.nb_count),
-                   _ptr(r.nb_fprint),
+                   _ptr(r.nb_fprint), _ptr(r.nb_band), _ptr(r.nb_band_ids),
                    _ptr(r.keys_g), _ptr(r.keys_d), _ptr(r.perm_g), _ptr(r.perm_d),
                    _ptr(r.cstart_g), _ptr(r.cstart_d), 0)
     g3 = (C.c_double * 3)(*[float(g[k]) if k < len(g) else 0.0 for k in range(3)])
@@ -320,6 +358,27 @@ def run(p: Params, s: State, tau: float, nsteps: int, g=(0.0, 0.0, 0.0), scheme:
         else:
             step_x(p, s, tau, g, scheme)
     return s
+
+
+def dust_profile(p: Params, x, m: float, nbins):
+    """Cloud-in-cell binned density of particles of mass m at x (dim, n) on
+    nbins bins per axis over the box; array of shape nbins[::-1] flattened
+    with axis 0 fastest (bin b = i0 + nb0 (i1 + nb1 i2))."""
+    x = _f64(x, (p.dim, -1))
+    n = x.shape[1]
+    nb = (C.c_int32 * 3)(*[int(nbins[k]) if k < p.dim else 1 for k in range(3)])
+    total = int(np.prod([nb[k] for k in range(p.dim)]))
+    rho = np.zeros(total)
+    pc = p.c()
+    rc = _load().orc_dust_profile(C.byref(pc), nb, n, _ptr(x), float(m), _ptr(rho))
+    if rc != 0:
+        raise ValueError("orc_dust_profile: bad bin counts")
+    return rho
+
+
+def set_threads(n: int) -> int:
+    """Threads of the oracle's OpenMP loops from now on; returns the count in use."""
+    return int(_load().orc_set_threads(int(n)))
 
 
 def omp_threads() -> int:

@@ -34,17 +34,22 @@
  *   - particles are ordered by (cell key, particle id).
  *
  * Cell keys and neighbour membership are integer decisions taken from
- * floating point. They are made in the precision of the path under test
- * (binary32 when decide_fp32 = 1, binary64 otherwise), so both sides take
- * the same decision; every value is then computed in binary64.
+ * floating point. Both are taken exactly, over the real numbers, from their
+ * definitions (orc_axis_cell, orc_pair_band); every value is computed in
+ * binary64. Pairs within a few units in the last place of the support
+ * radius, in the precision of the path under test (path_fp32), are flagged
+ * so that a checker can report them instead of failing on them.
  *
- * Build with -ffp-contract=off so that the binary32 decisions are plain
- * IEEE operations (no fused multiply-add).
+ * Build with -ffp-contract=off so that every binary64 expression is rounded
+ * as written (no fused multiply-add).
  */
 #include <math.h>
 #include <stdint.h>
 #include <stdlib.h>
 #include <string.h>
+#ifdef _OPENMP
+#include <omp.h>
+#endif
 
 #define ORC_OK 0
 #define ORC_E_ARG 1
@@ -52,7 +57,7 @@
 
 typedef struct {
     int32_t dim;          /* 1, 2 or 3 */
-    int32_t decide_fp32;  /* 1: keys and neighbour membership in binary32 */
+    int32_t path_fp32;    /* 1: the path under test computes in binary32 (width of the reported pair band) */
     int32_t eos;          /* 0 isothermal, 1 adiabatic */
     int32_t tstar_mode;   /* 0 arithmetic mean of t_j, 1 harmonic mean */
     int32_t periodic[3];
@@ -112,23 +117,103 @@ int orc_ncell(const orc_params *P, int32_t ncell[3])
     return ORC_OK;
 }
 
-/* Cell coordinate of one position along axis d, clamped to [0, n-1]. */
+/* ------------------------------------------------------------------------ */
+/* Integer decisions, taken exactly from their definitions.                 */
+/*                                                                          */
+/* A cell index and a neighbour membership are integers decided from        */
+/* floating-point data. Both are decided here over the real numbers, on the */
+/* stored values (the binary32 positions of the FP32 path are exact         */
+/* binary64 values):                                                        */
+/*   cell index along axis d: floor((x - lo) n / L), L = hi - lo in         */
+/*     binary64, clamped to [0, n-1] (Sec. 2.3: disjoint volumes);          */
+/*   membership: r^2 < 4 h^2 with r^2 = sum over axes of s^2, s = x_a - x_b */
+/*     shifted by -+L when |x_a - x_b| > L/2 on a periodic axis (support of */
+/*     the kernel in the sums of Eq. 19).                                   */
+/* A binary64 estimate settles every case whose margin exceeds the          */
+/* estimate's rounding error; the others are settled with integers.         */
+/* ------------------------------------------------------------------------ */
+
+/* |v| = m 2^e with an integer m < 2^53 (m = 0 for v = 0). */
+static void orc_split(double v, uint64_t *m, int *e)
+{
+    int ex = 0;
+    double f = frexp(fabs(v), &ex); /* |v| = f 2^ex, 1/2 <= f < 1 */
+    *m = (uint64_t)ldexp(f, 53);
+    *e = ex - 53;
+}
+
+/* Multi-word two's-complement integer, value = sum_j w[j] 2^(32 j + E0).   */
+/* Every binary64 value times an integer below 2^31 is an integer multiple  */
+/* of 2^E0 (E0 = -1126, the last bit of the smallest subnormal written with */
+/* a 53-bit m) below 2^(1024 + 31); 72 words hold a sum of three of them.   */
+#define ORC_BN_WORDS 72
+#define ORC_BN_E0 (-1126)
+typedef struct {
+    uint32_t w[ORC_BN_WORDS];
+} orc_bn;
+
+/* A += m k 2^e (negative = 0) or A -= m k 2^e (negative = 1); m < 2^53, k < 2^31. */
+static void orc_bn_add(orc_bn *A, int negative, uint64_t m, uint64_t k, int e)
+{
+    int s = e - ORC_BN_E0;
+    unsigned __int128 t = ((unsigned __int128)m * k) << (s % 32); /* < 2^115 */
+    uint32_t add[ORC_BN_WORDS];
+    memset(add, 0, sizeof add);
+    for (int j = 0; j < 4; ++j) add[s / 32 + j] = (uint32_t)(t >> (32 * j));
+    int64_t carry = 0;
+    for (int j = 0; j < ORC_BN_WORDS; ++j) {
+        int64_t v = (int64_t)A->w[j] + (negative ? -(int64_t)add[j] : (int64_t)add[j]) + carry;
+        A->w[j] = (uint32_t)v;                                     /* v mod 2^32 */
+        carry = (v - (int64_t)(uint32_t)v) / ((int64_t)1 << 32);   /* exact */
+    }
+}
+
+static int orc_bn_sign(const orc_bn *A)
+{
+    if (A->w[ORC_BN_WORDS - 1] & 0x80000000u) return -1;
+    for (int j = 0; j < ORC_BN_WORDS; ++j)
+        if (A->w[j]) return 1;
+    return 0;
+}
+
+/* A += sign * v * k for a binary64 v and an integer 0 <= k < 2^31. */
+static void orc_bn_term(orc_bn *A, double v, int64_t k, int sign)
+{
+    uint64_t m;
+    int e;
+    orc_split(v, &m, &e);
+    orc_bn_add(A, (v < 0.0) != (sign < 0), m, (uint64_t)k, e);
+}
+
+/* Sign of (x - lo) n - i L over the reals: where x lies against the face   */
+/* between cells i - 1 and i.                                               */
+static int orc_face_sign(double x, double lo, double L, int64_t n, int64_t i)
+{
+    orc_bn A;
+    memset(&A, 0, sizeof A);
+    orc_bn_term(&A, x, n, +1);
+    orc_bn_term(&A, lo, n, -1);
+    orc_bn_term(&A, L, i, -1);
+    return orc_bn_sign(&A);
+}
+
+/* Cell index of one position along axis d: floor((x - lo) n / L), clamped */
+/* to [0, n-1]; NaN goes to cell 0.                                          */
 static int64_t orc_axis_cell(const orc_params *P, int d, int32_t n, double x)
 {
-    double t;
-    if (P->decide_fp32) {
-        float inv = (float)((double)n / (P->hi[d] - P->lo[d]));
-        float xf = (float)x;
-        float lof = (float)P->lo[d];
-        float tf = (xf - lof) * inv;
-        t = floor((double)tf);
-    } else {
-        double inv = (double)n / (P->hi[d] - P->lo[d]);
-        t = floor((x - P->lo[d]) * inv);
-    }
-    if (t < 0.0) t = 0.0;
-    if (t > (double)(n - 1)) t = (double)(n - 1);
-    return (int64_t)t;
+    if (x != x) return 0;
+    if (isinf(x)) return x > 0.0 ? n - 1 : 0;
+    double lo = P->lo[d], L = P->hi[d] - P->lo[d];
+    /* estimate: three correctly rounded operations, relative error below 2^-50 */
+    double q = (x - lo) * (double)n / L;
+    double f = floor(q);
+    int64_t i = !(f >= 0.0) ? 0 : (f > (double)(n - 1) ? n - 1 : (int64_t)f);
+    /* no integer within the estimate's error: its floor is the exact one */
+    if (fabs(q - nearbyint(q)) > 1e-12 * (1.0 + fabs(q))) return i;
+    /* otherwise settle the cell face exactly */
+    while (i > 0 && orc_face_sign(x, lo, L, n, i) < 0) --i;
+    while (i < n - 1 && orc_face_sign(x, lo, L, n, i + 1) >= 0) ++i;
+    return i;
 }
 
 /* key = ix + nx (iy + ny iz); x is the position of one particle, x[d]. */
@@ -139,76 +224,141 @@ static int64_t orc_key(const orc_params *P, const int32_t nc[3], const double x[
     return c[0] + (int64_t)nc[0] * (c[1] + (int64_t)nc[1] * c[2]);
 }
 
-/* ------------------------------------------------------------------------ */
-/* Pair geometry. Membership r^2 < (2h)^2 decided in the path's precision,  */
-/* with r^2 = fma(dz, dz, fma(dy, dy, dx * dx)) (one rounding per term).     */
-/* d[] receives x_a - x_b (minimum image on periodic axes) in binary64.      */
-/*                                                                          */
-/* The decision's displacement along an axis is s = x_a - x_b; when |s|     */
-/* exceeds half the box, the image shift is applied to s (exact: s and L    */
-/* are within a factor of two) and the rounding error of s, recovered with  */
-/* Knuth's two-sum, is added back, so that pairs across the periodic seam   */
-/* lose no more precision than any other pair.                              */
-/* ------------------------------------------------------------------------ */
-static float orc_disp32(float xa, float xb, int per, float L, float half)
+/* |v| = m 2^e with an odd integer m (m = 0 for v = 0): e is v's last bit. */
+static void orc_split_odd(double v, uint64_t *m, int *e)
 {
-    float s = xa - xb;
-    if (per && (s > half || s < -half)) {
-        float bb = s - xa;
-        float e = (xa - (s - bb)) + (-xb - bb);
-        float t = s > half ? s - L : s + L;
-        return t + e;
+    orc_split(v, m, e);
+    while (*m && !(*m & 1u)) {
+        *m >>= 1;
+        *e += 1;
     }
-    return s;
 }
 
-static double orc_disp64(double xa, double xb, int per, double L, double half)
+static int orc_bits(uint64_t m)
 {
-    double s = xa - xb;
-    if (per && (s > half || s < -half)) {
-        double bb = s - xa;
-        double e = (xa - (s - bb)) + (-xb - bb);
-        double t = s > half ? s - L : s + L;
-        return t + e;
+    int b = 0;
+    while (m) {
+        ++b;
+        m >>= 1;
     }
-    return s;
+    return b;
 }
 
-static int orc_pair(const orc_params *P, const double xa[3], const double xb[3],
-                    double d[3], double *r2)
+/* r^2 < 4 h^2 over the reals for the periodic image shifts chosen (shift[k] */
+/* L subtracted along axis k), with 128-bit integers: every coordinate, box */
+/* edge and h is an integer multiple of 2^g, g the smallest last bit among  */
+/* them. Returns 1 or 0, or -1 when the scaled values do not fit.           */
+static int orc_exact_lt(const orc_params *P, const double xa[3], const double xb[3], const int shift[3])
 {
-    int inside;
-    if (P->decide_fp32) {
-        float acc = 0.0f;
-        for (int k = 0; k < P->dim; ++k) {
-            float L = (float)(P->hi[k] - P->lo[k]);
-            float half = (float)(0.5 * (P->hi[k] - P->lo[k]));
-            float dx = orc_disp32((float)xa[k], (float)xb[k], P->periodic[k], L, half);
-            acc = (k == 0) ? dx * dx : fmaf(dx, dx, acc);
+    uint64_t mh;
+    int eh;
+    orc_split_odd(P->h, &mh, &eh);
+    uint64_t m[3][3];
+    int e[3][3], neg[3][3];
+    int g = eh;
+    for (int k = 0; k < P->dim; ++k) {
+        double v[3] = {xa[k], -xb[k], -(double)shift[k] * (P->hi[k] - P->lo[k])};
+        for (int t = 0; t < 3; ++t) {
+            orc_split_odd(v[t], &m[k][t], &e[k][t]);
+            neg[k][t] = v[t] < 0.0;
+            if (m[k][t] && e[k][t] < g) g = e[k][t];
         }
-        float lim = (float)(4.0 * P->h * P->h);
-        inside = acc < lim;
-    } else {
-        double acc = 0.0;
-        for (int k = 0; k < P->dim; ++k) {
-            double L = P->hi[k] - P->lo[k];
-            double half = 0.5 * (P->hi[k] - P->lo[k]);
-            double dx = orc_disp64(xa[k], xb[k], P->periodic[k], L, half);
-            acc = (k == 0) ? dx * dx : fma(dx, dx, acc);
-        }
-        inside = acc < 4.0 * P->h * P->h;
     }
-    double s = 0.0;
+    unsigned __int128 r2 = 0;
+    for (int k = 0; k < P->dim; ++k) {
+        __int128 S = 0;
+        for (int t = 0; t < 3; ++t) {
+            if (!m[k][t]) continue;
+            int sh = e[k][t] - g;
+            if (orc_bits(m[k][t]) + sh > 124) return -1;
+            __int128 term = (__int128)((unsigned __int128)m[k][t] << sh);
+            S += neg[k][t] ? -term : term;
+        }
+        if (S < 0) S = -S;
+        if (S >= ((__int128)1 << 62)) return -1;
+        r2 += (unsigned __int128)S * (unsigned __int128)S;
+    }
+    /* 4 h^2 = mh^2 2^(2 (eh - g) + 2) */
+    int sh = 2 * (eh - g) + 2;
+    if (2 * orc_bits(mh) + sh > 127) return -1;
+    unsigned __int128 H = ((unsigned __int128)mh * mh) << sh;
+    return r2 < H;
+}
+
+/* Neighbour decision of a pair: 1 if r^2 < 4 h^2 over the reals, else 0.   */
+/* d[] receives x_a - x_b (minimum image on periodic axes) and *r2 its      */
+/* squared norm, in binary64. *band is set when r^2 lies within 8 units in  */
+/* the last place of 4 h^2, in the precision of the path under test, of    */
+/* 4 h^2 (the GPU path may decide such a pair either way; the kernel there  */
+/* is below 1e-17 of its peak), or when the decision could not be          */
+/* certified (the 128-bit form overflows: only for a coordinate within      */
+/* about 2^-15 of zero in a pair within 2^-49 of the boundary).            */
+static int orc_pair_band(const orc_params *P, const double xa[3], const double xb[3], double d[3], double *r2,
+                         int *band)
+{
+    const double u = 0x1p-53;
+    int shift[3] = {0, 0, 0};
+    double slack = 0.0; /* an image choice within rounding of L/2 */
+    double s2 = 0.0;
     for (int k = 0; k < 3; ++k) {
         d[k] = 0.0;
         if (k >= P->dim) continue;
         double L = P->hi[k] - P->lo[k];
-        double dx = orc_disp64(xa[k], xb[k], P->periodic[k], L, 0.5 * L);
-        d[k] = dx;
-        s += dx * dx;
+        double s = xa[k] - xb[k];
+        if (P->periodic[k]) {
+            if (fabs(fabs(s) - 0.5 * L) <= 4.0 * u * L) slack += 32.0 * u * L * L;
+            if (s > 0.5 * L) {
+                s -= L;
+                shift[k] = 1;
+            } else if (s < -0.5 * L) {
+                s += L;
+                shift[k] = -1;
+            }
+        }
+        d[k] = s;
+        s2 += s * s;
     }
-    *r2 = s;
-    return inside;
+    *r2 = s2;
+    const double H = 4.0 * P->h * P->h;
+    const double err = 16.0 * u * (s2 + H) + slack; /* bounds |s2 - r^2| + |H - 4h^2| */
+    const double ulp_path = ldexp(1.0, ilogb(H) - (P->path_fp32 ? 23 : 52));
+    *band = fabs(s2 - H) <= 8.0 * ulp_path + err;
+    if (fabs(s2 - H) > err) return s2 < H;
+    int exact = slack > 0.0 ? -1 : orc_exact_lt(P, xa, xb, shift);
+    if (exact < 0) {
+        *band = 1;
+        return s2 < H;
+    }
+    return exact;
+}
+
+static int orc_pair(const orc_params *P, const double xa[3], const double xb[3], double d[3], double *r2)
+{
+    int band;
+    return orc_pair_band(P, xa, xb, d, r2, &band);
+}
+
+/* The membership decision of one pair, for the tests: 1 if r^2 < 4 h^2, else */
+/* 0; *band as in orc_pair_band.                                              */
+int orc_neighbour(const orc_params *P, const double *xa, const double *xb, int32_t *band)
+{
+    double pa[3] = {0, 0, 0}, pb[3] = {0, 0, 0}, d[3], r2;
+    int b = 0;
+    for (int k = 0; k < P->dim; ++k) {
+        pa[k] = xa[k];
+        pb[k] = xb[k];
+    }
+    int in = orc_pair_band(P, pa, pb, d, &r2, &b);
+    if (band) *band = b;
+    return in;
+}
+
+/* The cell index of one position along axis d, for the tests. */
+int64_t orc_cell_index(const orc_params *P, int d, double x)
+{
+    int32_t nc[3];
+    orc_ncell(P, nc);
+    return orc_axis_cell(P, d, nc[d], x);
 }
 
 /* ------------------------------------------------------------------------ */
@@ -327,9 +477,13 @@ static void orc_foreach_candidate(const orc_grid *G, const double p[3],
 
 /* ------------------------------------------------------------------------ */
 /* Summation density rho_a = sum_b m W(|r_ab|, h), self term included.       */
-/* Also the neighbour count and an order-free fingerprint of the neighbour   */
-/* set: sum over neighbours of (id_b + 1) * 0x9E3779B97F4A7C15 mod 2^64.     */
+/* Also the neighbour statistics a checker compares with: the count and an  */
+/* order-free fingerprint of the neighbours outside the reported band (sum  */
+/* over them of (id_b + 1) * 0x9E3779B97F4A7C15 mod 2^64), the number of    */
+/* candidate pairs inside the band and the ids of the first ORC_NBAND.      */
 /* ------------------------------------------------------------------------ */
+#define ORC_NBAND 4
+
 typedef struct {
     const orc_grid *G;
     double pa[3];
@@ -337,15 +491,24 @@ typedef struct {
     double rho;
     int64_t count;
     uint64_t fprint;
+    int64_t nband;
+    int64_t band_id[ORC_NBAND];
 } orc_dens_ctx;
 
 static void orc_dens_visit(void *vctx, int64_t b)
 {
     orc_dens_ctx *c = (orc_dens_ctx *)vctx;
     double pb[3], d[3], r2;
+    int band = 0;
     orc_get_pos(c->G->P->dim, c->G->n, c->G->x, b, pb);
-    if (!orc_pair(c->G->P, c->pa, pb, d, &r2)) return;
+    int inside = orc_pair_band(c->G->P, c->pa, pb, d, &r2, &band);
+    if (band) {
+        if (c->nband < ORC_NBAND) c->band_id[c->nband] = b;
+        c->nband += 1;
+    }
+    if (!inside) return;
     c->rho += c->m * orc_W(c->G->P->dim, c->G->P->h, sqrt(r2));
+    if (band) return;
     c->count += 1;
     c->fprint += (uint64_t)(b + 1) * 0x9E3779B97F4A7C15ull;
 }
@@ -368,8 +531,10 @@ static int orc_make_grid(const orc_params *P, int64_t n, const double *x, orc_gr
 }
 
 /* Density of one particle set (gas or dust) of particle mass m. */
+/* count, fprint, nband (each [n]) and band_ids ([ORC_NBAND n], -1 beyond  */
+/* nband) are nullable.                                                     */
 int orc_density(const orc_params *P, int64_t n, const double *x, double m,
-                double *rho, int64_t *count, uint64_t *fprint)
+                double *rho, int64_t *count, uint64_t *fprint, int64_t *nband, int64_t *band_ids)
 {
     orc_grid G;
     int64_t *perm = NULL, *cstart = NULL;
@@ -383,10 +548,15 @@ int orc_density(const orc_params *P, int64_t n, const double *x, double m,
         c.rho = 0.0;
         c.count = 0;
         c.fprint = 0;
+        c.nband = 0;
+        for (int k = 0; k < ORC_NBAND; ++k) c.band_id[k] = -1;
         orc_foreach_candidate(&G, c.pa, orc_dens_visit, &c);
         rho[a] = c.rho;
         if (count) count[a] = c.count;
         if (fprint) fprint[a] = c.fprint;
+        if (nband) nband[a] = c.nband;
+        if (band_ids)
+            for (int k = 0; k < ORC_NBAND; ++k) band_ids[(int64_t)ORC_NBAND * a + k] = c.band_id[k];
     }
     free(perm);
     free(cstart);
@@ -564,8 +734,10 @@ typedef struct {
     double *acc_g;          /* [dim*ng] pressure (+viscous) acceleration */
     double *dedt_g;         /* [ng] */
     double *acc_scale_g;    /* [ng] magnitude sum of the pair terms of A (diagnostic) */
-    int64_t *nb_count;      /* [ng] */
-    uint64_t *nb_fprint;    /* [ng] */
+    int64_t *nb_count;      /* [ng] neighbours outside the reported band */
+    uint64_t *nb_fprint;    /* [ng] their fingerprint */
+    int64_t *nb_band;       /* [ng] candidate pairs inside the band */
+    int64_t *nb_band_ids;   /* [ORC_NBAND ng] ids of the first of them, -1 beyond */
     int64_t *keys_g, *keys_d;     /* [ng], [nd] per particle (id order) */
     int64_t *perm_g, *perm_d;     /* [ng], [nd] id at sorted slot */
     int64_t *cstart_g, *cstart_d; /* [ncells+1] */
@@ -612,7 +784,8 @@ int orc_step(const orc_params *P, int64_t ng, int64_t nd,
 
     /* 2. Gas summation density and pressure. */
     if (ng > 0) orc_density(P, ng, gx, P->m_gas, rho, out ? out->nb_count : NULL,
-                            out ? out->nb_fprint : NULL);
+                            out ? out->nb_fprint : NULL, out ? out->nb_band : NULL,
+                            out ? out->nb_band_ids : NULL);
 
     /* 3. Gas pressure (+ viscous) acceleration and energy rate. */
     if (ng > 0) orc_accel(P, ng, gx, gv, ge, rho, acc, dedt, out ? out->acc_scale_g : NULL);
@@ -962,8 +1135,8 @@ int orc_step_x(const orc_params *P, int scheme, int64_t ng, int64_t nd,
         goto done;
     }
     /* densities, pressure and the gas pressure force */
-    if (ng > 0) orc_density(P, ng, gx, P->m_gas, rho_g, NULL, NULL);
-    if (nd > 0) orc_density(P, nd, dx, P->m_dust, rho_d, NULL, NULL);
+    if (ng > 0) orc_density(P, ng, gx, P->m_gas, rho_g, NULL, NULL, NULL, NULL);
+    if (nd > 0) orc_density(P, nd, dx, P->m_dust, rho_d, NULL, NULL, NULL, NULL);
     if (ng > 0) orc_accel(P, ng, gx, gv, ge, rho_g, acc, dedt, ascale);
     for (int64_t a = 0; a < ng; ++a) {
         q[a] = orc_pressure(P, rho_g[a], ge ? ge[a] : 0.0) / (rho_g[a] * rho_g[a]);
@@ -1126,4 +1299,81 @@ done:
     free(Sg); free(Sd); free(Ad); free(ASd); free(rdg); free(Kg); free(rgd); free(inv_t); free(inv_rho);
     free(pg); free(cg); free(pd); free(cd);
     return rc;
+}
+
+/* ------------------------------------------------------------------------ */
+/* Binned dust density (the profile the differentiable rollout's loss is    */
+/* taken on; the paper's test problems compare dust-density profiles,       */
+/* Sec. 3). Cloud in cell on nbins[k] bins per axis over the box: a         */
+/* particle's mass goes to the two bin centres that bracket it along each   */
+/* axis, in proportion to its nearness (linear weights), with the product   */
+/* of the per-axis weights in 2D and 3D; bin indices wrap on periodic axes  */
+/* and are clamped to the end bins on walled axes. rho = mass / bin volume. */
+/* ------------------------------------------------------------------------ */
+int orc_dust_profile(const orc_params *P, const int32_t nbins[3], int64_t n, const double *x, double m,
+                     double *rho)
+{
+    int64_t nb[3] = {1, 1, 1};
+    double width[3] = {1.0, 1.0, 1.0};
+    int64_t total = 1;
+    double vol = 1.0;
+    for (int k = 0; k < P->dim; ++k) {
+        if (nbins[k] < 1) return ORC_E_ARG;
+        nb[k] = nbins[k];
+        width[k] = (P->hi[k] - P->lo[k]) / (double)nb[k];
+        total *= nb[k];
+        vol *= width[k];
+    }
+    for (int64_t b = 0; b < total; ++b) rho[b] = 0.0;
+    for (int64_t j = 0; j < n; ++j) {
+        int64_t lower[3] = {0, 0, 0}, upper[3] = {0, 0, 0};
+        double wl[3] = {1.0, 1.0, 1.0}, wu[3] = {0.0, 0.0, 0.0};
+        int skip = 0;
+        for (int k = 0; k < P->dim; ++k) {
+            double xk = x[(int64_t)k * n + j];
+            if (xk != xk) skip = 1;
+            if (skip) break;
+            /* position in units of bins, measured from the first bin centre */
+            double s = (xk - P->lo[k]) / width[k] - 0.5;
+            double below = floor(s);
+            double frac = s - below;
+            int64_t i0 = (int64_t)below, i1 = i0 + 1;
+            if (P->periodic[k]) {
+                i0 = ((i0 % nb[k]) + nb[k]) % nb[k];
+                i1 = ((i1 % nb[k]) + nb[k]) % nb[k];
+            } else {
+                i0 = i0 < 0 ? 0 : (i0 > nb[k] - 1 ? nb[k] - 1 : i0);
+                i1 = i1 < 0 ? 0 : (i1 > nb[k] - 1 ? nb[k] - 1 : i1);
+            }
+            lower[k] = i0;
+            upper[k] = i1;
+            wl[k] = 1.0 - frac;
+            wu[k] = frac;
+        }
+        if (skip) continue;
+        for (int cz = 0; cz < (P->dim > 2 ? 2 : 1); ++cz)
+            for (int cy = 0; cy < (P->dim > 1 ? 2 : 1); ++cy)
+                for (int cx = 0; cx < 2; ++cx) {
+                    int64_t bx = cx ? upper[0] : lower[0];
+                    int64_t by = cy ? upper[1] : lower[1];
+                    int64_t bz = cz ? upper[2] : lower[2];
+                    double wgt = (cx ? wu[0] : wl[0]) * (cy ? wu[1] : wl[1]) * (cz ? wu[2] : wl[2]);
+                    rho[bx + nb[0] * (by + nb[1] * bz)] += m * wgt;
+                }
+    }
+    for (int64_t b = 0; b < total; ++b) rho[b] /= vol;
+    return ORC_OK;
+}
+
+/* Threads of the OpenMP loops (n >= 1); returns the number now in use. For
+ * timing the oracle on one core and on all cores. */
+int orc_set_threads(int n)
+{
+#ifdef _OPENMP
+    if (n >= 1) omp_set_num_threads(n);
+    return omp_get_max_threads();
+#else
+    (void)n;
+    return 1;
+#endif
 }

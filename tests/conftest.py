@@ -21,7 +21,7 @@ def oracle_params(w, **overrides):
     d = dict(dim=q["dim"], lo=q["lo"], hi=q["hi"], periodic=q["periodic"], h=q["h"],
              cell_size=q["cell_size"], m_gas=q["m_gas"], m_dust=q["m_dust"], eos=q["eos"],
              cs=q["cs"], gamma=q["gamma"], av_alpha=q["av_alpha"], av_beta=q["av_beta"],
-             tstar_mode=q["tstar_mode"], decide_fp32=1 if int(q["precision"]) == 0 else 0)
+             tstar_mode=q["tstar_mode"], path_fp32=1 if int(q["precision"]) == 0 else 0)
     d.update(overrides)
     return oracle.Params(**d)
 

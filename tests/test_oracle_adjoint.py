@@ -82,3 +82,47 @@ def test_torch_step_gradients_equal_finite_differences(orc):
                 fd = (lp - lm) / (2 * eps)
                 ad = float(grad.numpy().reshape(-1)[i])
                 assert abs(fd - ad) <= 1e-6 * (1.0 + abs(fd)), (name, i, fd, ad)
+
+
+# --------------------------------------------------------------------------
+# Binned dust density (cloud in cell): the profile the rollout's loss is on
+# --------------------------------------------------------------------------
+def test_dust_profile_weights_by_hand(orc):
+    """One particle at a bin centre puts its whole mass in that bin; one a
+    quarter of the way between two centres splits it 3/4 : 1/4 along that
+    axis (the product of per-axis splits in 2D); walled axes keep the mass in
+    the end bins, periodic axes wrap it to the far end."""
+    p = orc.Params(dim=2, lo=(0.0, 0.0), hi=(1.0, 2.0), periodic=(1, 0), h=0.1, cell_size=0.1, m_gas=1.0,
+                   m_dust=1.0)
+    nb = (4, 8)            # bins 0.25 x 0.25
+    vol = 0.25 * 0.25
+    rho = orc.dust_profile(p, np.array([[0.375], [1.125]]), 2.0, nb).reshape(8, 4)
+    want = np.zeros((8, 4))
+    want[4, 1] = 2.0 / vol
+    assert np.array_equal(rho, want)
+    # x at 0.375 + 0.0625 (a quarter of the way to the next centre), y at 0.125 - 0.0625 below the first centre
+    rho = orc.dust_profile(p, np.array([[0.4375], [0.0625]]), 1.0, nb).reshape(8, 4)
+    want = np.zeros((8, 4))
+    want[0, 1] = 0.75 / vol
+    want[0, 2] = 0.25 / vol
+    np.testing.assert_allclose(rho, want, rtol=1e-15, atol=0)
+    # across the periodic seam in x: 0.0625 lies between the centre of the last bin (0.875, wrapped) and the first
+    rho = orc.dust_profile(p, np.array([[0.0625], [1.125]]), 1.0, nb).reshape(8, 4)
+    want = np.zeros((8, 4))
+    want[4, 0] = 0.75 / vol
+    want[4, 3] = 0.25 / vol
+    np.testing.assert_allclose(rho, want, rtol=1e-15, atol=0)
+
+
+@pytest.mark.parametrize("dim", [1, 2, 3])
+def test_dust_profile_conserves_mass(orc, dim):
+    """sum_b rho_b V = n m for any positions, inside or beyond walled edges."""
+    rng = np.random.default_rng(40 + dim)
+    lo, hi = (0.0, -1.0, 0.5)[:dim], (1.0, 0.5, 2.0)[:dim]
+    p = orc.Params(dim=dim, lo=lo, hi=hi, periodic=(1, 0, 1)[:dim], h=0.1, cell_size=0.1, m_gas=1.0, m_dust=1.0)
+    nb = (7, 5, 6)[:dim]
+    x = np.stack([rng.uniform(lo[k] - 0.2, hi[k] + 0.2, 3000) for k in range(dim)])
+    rho = orc.dust_profile(p, x, 0.37, nb)
+    vol = np.prod([(hi[k] - lo[k]) / nb[k] for k in range(dim)])
+    assert abs(rho.sum() * vol - 3000 * 0.37) < 1e-10
+    assert rho.size == int(np.prod(nb)) and np.all(rho >= 0)

@@ -10,6 +10,7 @@ oracle's step.
 import json
 import math
 import os
+from fractions import Fraction
 
 import numpy as np
 import pytest
@@ -50,7 +51,7 @@ def test_kernel_derivative_matches_finite_difference(orc, dim):
 def test_binning_invariants(orc, fp32):
     rng = np.random.default_rng(11)
     p = orc.Params(dim=3, lo=(-0.5, 0.0, 2.0), hi=(0.5, 2.0, 3.0), periodic=(1, 0, 1), h=0.05,
-                   cell_size=0.1, m_gas=1.0, m_dust=1.0, decide_fp32=fp32)
+                   cell_size=0.1, m_gas=1.0, m_dust=1.0, path_fp32=fp32)
     x = np.stack([rng.uniform(-0.5, 0.5, 3000), rng.uniform(0.0, 2.0, 3000), rng.uniform(2.0, 3.0, 3000)])
     if fp32:
         x = x.astype(np.float32).astype(np.float64)
@@ -69,6 +70,109 @@ def test_binning_invariants(orc, fp32):
         w = (p.hi[d] - p.lo[d]) / nc[d]
         lo = p.lo[d] + c[d] * w
         assert np.all(x[d] >= lo - 1e-6) and np.all(x[d] < lo + w + 1e-6)
+
+
+# --------------------------------------------------------------------------
+# Integer decisions against exact rational arithmetic
+# --------------------------------------------------------------------------
+def _exact_cell(x, lo, hi, n):
+    """floor((x - lo) n / L) over the rationals, L = hi - lo in binary64, clamped."""
+    L = Fraction(float(hi) - float(lo))
+    q = (Fraction(float(x)) - Fraction(float(lo))) * n / L
+    return min(max(math.floor(q), 0), n - 1)
+
+
+@pytest.mark.parametrize("fp32", [0, 1])
+def test_cell_keys_exact_at_faces(orc, fp32):
+    """Positions on, and one or two ulp either side of, every cell face (all
+    faces, or 400 of them for fine grids) of four grids whose cell widths are
+    not powers of two: the oracle's cell index equals floor((x - lo) n / L)
+    computed with rationals. The rounded product a kernel might use instead,
+    floor(fl(fl(x - lo) fl(n / L))) in the path's precision, disagrees with
+    it on some of these positions, so an inexact rule in the oracle fails here."""
+    ft = np.float32 if fp32 else np.float64
+    naive_misses = 0
+    for lo, hi, cell in [(-0.3, 0.77, 0.07), (0.0, 1.0, 1.0 / 7.0), (0.0, 1.0, 5.4e-5), (2.0, 3.0, 0.1)]:
+        p = orc.Params(dim=1, lo=(lo,), hi=(hi,), periodic=(0,), h=cell, cell_size=cell, m_gas=1.0, m_dust=1.0,
+                       path_fp32=fp32)
+        n = orc.ncell(p)[0]
+        L = float(hi) - float(lo)
+        faces = range(0, n + 1) if n <= 400 else np.linspace(0, n, 400).astype(int)
+        xs = []
+        for k in faces:
+            v = ft(float(Fraction(lo) + Fraction(L) * k / n))
+            xs.append(v)
+            for _ in range(2):
+                xs.append(np.nextafter(xs[-1], ft(np.inf)))
+            w = v
+            for _ in range(2):
+                w = np.nextafter(w, ft(-np.inf))
+                xs.append(w)
+        for x in xs:
+            want = _exact_cell(x, lo, hi, n)
+            assert orc.cell_index(p, 0, float(x)) == want, (lo, hi, cell, float(x), want)
+            naive = math.floor(ft(ft(x - ft(lo)) * ft(n / L)))
+            naive_misses += min(max(naive, 0), n - 1) != want
+    assert naive_misses > 0
+
+
+def _exact_r2(xa, xb, lo, hi, periodic):
+    r2 = Fraction(0)
+    for k in range(len(xa)):
+        s = Fraction(float(xa[k])) - Fraction(float(xb[k]))
+        if periodic:
+            L = Fraction(float(hi[k]) - float(lo[k]))
+            if s > L / 2:
+                s -= L
+            elif s < -L / 2:
+                s += L
+        r2 += s * s
+    return r2
+
+
+@pytest.mark.parametrize("fp32", [0, 1])
+@pytest.mark.parametrize("periodic", [0, 1])
+def test_membership_exact_near_support_radius(orc, fp32, periodic):
+    """Pairs at distance 2h (1 + delta), delta from -1e-5 to 1e-5 down to a
+    few ulp, in random directions in 3D, on both sides of a periodic seam:
+    the oracle's membership is r^2 < 4h^2 over the rationals, and its band
+    flag covers every pair within 8 ulp (of 4h^2, in the path's precision) of
+    the boundary and no pair beyond that plus twice its binary64 estimate's
+    error."""
+    rng = np.random.default_rng(29 + 2 * fp32 + periodic)
+    ft = np.float32 if fp32 else np.float64
+    lo, hi, h = (0.0, 0.0, 0.0), (1.0, 1.0, 1.0), 0.0375
+    p = orc.Params(dim=3, lo=lo, hi=hi, periodic=(periodic,) * 3, h=h, cell_size=0.1, m_gas=1.0, m_dust=1.0,
+                   path_fp32=fp32)
+    H = 4 * Fraction(h) ** 2
+    ulp = Fraction(2) ** (math.floor(math.log2(float(H))) - (23 if fp32 else 52))
+    est_err = 32 * Fraction(2) ** -53 * H  # the oracle's binary64 estimate of r^2 - 4h^2 is this close
+    deltas = [s * d for s in (-1, 1) for d in (1e-5, 1e-6, 1e-7, 3e-8, 1e-8, 3e-9, 1e-10, 1e-12, 1e-14, 1e-15, 3e-16, 1e-16)]
+    inside_seen = band_seen = 0
+    for trial in range(288):
+        c = rng.uniform(0.02, 0.05, 3) if periodic else rng.uniform(0.3, 0.7, 3)
+        u = rng.normal(size=3)
+        u /= np.linalg.norm(u)
+        d = deltas[trial % len(deltas)]
+        b = c - 2 * h * (1 + d) * u * (1 if periodic else -1)
+        if periodic:
+            b = np.mod(b, 1.0)
+        xa, xb = c.astype(ft), b.astype(ft)
+        r2 = _exact_r2(xa, xb, lo, hi, periodic)
+        inside, band = orc.neighbour(p, xa.astype(np.float64), xb.astype(np.float64))
+        assert inside == (r2 < H), (trial, float(r2 - H))
+        if abs(r2 - H) <= 8 * ulp:
+            assert band
+        if abs(r2 - H) > 8 * ulp + 2 * est_err:
+            assert not band
+        inside_seen += inside
+        band_seen += band
+    assert 0 < inside_seen < 288 and band_seen > 0
+    # exactly on the boundary (2h = 1/8 is dyadic): not a neighbour; one ulp closer: a neighbour
+    p8 = orc.Params(dim=1, lo=(0.0,), hi=(1.0,), periodic=(0,), h=0.0625, cell_size=0.1, m_gas=1.0, m_dust=1.0,
+                    path_fp32=fp32)
+    assert orc.neighbour(p8, [0.5], [0.625]) == (False, True)
+    assert orc.neighbour(p8, [0.5], [float(np.nextafter(ft(0.625), ft(0)))]) == (True, True)
 
 
 # --------------------------------------------------------------------------
@@ -95,7 +199,7 @@ def test_cell_lists_equal_brute_force(orc, dim, periodic, fp32):
     h = {1: 0.01, 2: 0.04, 3: 0.09}[dim]
     common = dict(dim=dim, lo=lo, hi=hi, periodic=(periodic,) * dim, h=h, cell_size=1.7 * h,
                   m_gas=1.0 / n, m_dust=1.0, eos=1, gamma=1.4, av_alpha=1.0, av_beta=2.0,
-                  decide_fp32=fp32)
+                  path_fp32=fp32)
     pc = orc.Params(brute=0, **common)
     pb = orc.Params(brute=1, **common)
     rc, cc, fc = orc.density(pc, x, pc.m_gas)
