@@ -2,6 +2,7 @@
 // the single context and the batch.
 #include <cmath>
 #include <cstdio>
+#include <limits>
 #include <string>
 
 #include "tfsph_internal.cuh"
@@ -53,5 +54,73 @@ uint32_t cell_grid(const tfsph_params &p, int ncell[3])
     }
     return (uint32_t)nc;
 }
+
+namespace {
+
+// Error-free transformations in binary64, round to nearest: s + e = a + b
+// exactly (Knuth's two-sum) and p + e = a b exactly (the product's error by
+// one fused multiply-add).
+void two_sum(double a, double b, double &s, double &e)
+{
+    s = a + b;
+    const double bb = s - a;
+    e = (a - (s - bb)) + (b - bb);
+}
+
+void two_prod(double a, double b, double &p, double &e)
+{
+    p = a * b;
+    e = std::fma(a, b, -p);
+}
+
+// Sign of (x - lo) n - i L over the reals: where x lies against the face
+// between cells i - 1 and i. The six exact terms of the two-products are
+// summed into a nonoverlapping expansion (Shewchuk's grow-expansion), whose
+// largest nonzero component has the sign of the exact sum.
+int face_sign(double x, double lo, double L, int n, int i)
+{
+    double t[6];
+    two_prod(x, (double)n, t[0], t[1]);
+    two_prod(-lo, (double)n, t[2], t[3]);
+    two_prod(-(double)i, L, t[4], t[5]);
+    double g[6];
+    for (int k = 0; k < 6; ++k) {
+        double q = t[k];
+        for (int j = 0; j < k; ++j) {
+            double sum, err;
+            two_sum(q, g[j], sum, err);
+            g[j] = err;
+            q = sum;
+        }
+        g[k] = q;
+    }
+    for (int k = 5; k >= 0; --k)
+        if (g[k] != 0.0) return g[k] > 0.0 ? 1 : -1;
+    return 0;
+}
+
+}  // namespace
+
+template <class T> void face_thresholds(double lo, double hi, int n, T *thr)
+{
+    const double L = hi - lo;
+    const T inf = std::numeric_limits<T>::infinity();
+    thr[0] = -inf;
+    thr[n] = inf;
+    for (int i = 1; i < n; ++i) {
+        T f = (T)(lo + (double)i * (L / (double)n));  // within an ulp or two of the face
+        // up while f lies below the face, then down while the next value below does not
+        for (int k = 0; k < 64 && face_sign((double)f, lo, L, n, i) < 0; ++k) f = std::nextafter(f, inf);
+        for (int k = 0; k < 64; ++k) {
+            const T below = std::nextafter(f, -inf);
+            if (face_sign((double)below, lo, L, n, i) < 0) break;
+            f = below;
+        }
+        thr[i] = f;
+    }
+}
+
+template void face_thresholds<float>(double, double, int, float *);
+template void face_thresholds<double>(double, double, int, double *);
 
 }  // namespace tfsph

@@ -116,6 +116,27 @@ template <class T> void build_geo(tfsph_ctx *c)
     memcpy(c->phys, &Ph, sizeof(Ph));
 }
 
+// Device table of the exact cell-face thresholds of every axis (cell_key);
+// the geometry's per-axis pointers are set into it.
+template <class T> int upload_thresholds(tfsph_ctx *c)
+{
+    Geo<T> &G = *reinterpret_cast<Geo<T> *>(c->geo);
+    size_t off[3] = {0, 0, 0}, total = 0;
+    for (int d = 0; d < c->dim; ++d) {
+        off[d] = total;
+        total += (size_t)G.n[d] + 1;
+    }
+    std::vector<T> h(total);
+    for (int d = 0; d < c->dim; ++d) face_thresholds<T>(c->p.lo[d], c->p.hi[d], G.n[d], h.data() + off[d]);
+    void *dev = nullptr;
+    int rc = dalloc(c, &dev, total * sizeof(T));
+    if (rc) return rc;
+    cudaError_t e = cudaMemcpy(dev, h.data(), total * sizeof(T), cudaMemcpyHostToDevice);
+    if (e != cudaSuccess) return cuda_fail(c, e, "cudaMemcpy");
+    for (int d = 0; d < c->dim; ++d) G.thr[d] = static_cast<const T *>(dev) + off[d];
+    return TFSPH_OK;
+}
+
 LaunchCtx lctx(const tfsph_ctx *c)
 {
     LaunchCtx L;
@@ -399,6 +420,8 @@ int tfsph_init(tfsph_ctx **out, const tfsph_params *p, const void *const *gas, i
     cudaError_t e = cudaGetDevice(&c->device);
     if (e != cudaSuccess) return bail(cuda_fail(c, e, "cudaGetDevice"));
 
+    if ((rc = p->precision == TFSPH_FP64 ? upload_thresholds<double>(c) : upload_thresholds<float>(c)))
+        return bail(rc);
     const size_t v4 = 4 * c->tsize;
     PhaseBufs *ph[2] = {&c->G, &c->D};
     for (PhaseBufs *P : ph) {

@@ -70,7 +70,21 @@ template <class T> struct Geo {
     T inv_h;
     T h;
     uint32_t ncells;
+    // exact cell index (cell_key): per axis, n + 1 device values; thr[d][i]
+    // (0 < i < n) is the smallest T value at or above the face lo + i L / n
+    // between cells i - 1 and i (real arithmetic, L = hi - lo in binary64),
+    // so that for a stored coordinate x, x >= face i exactly when
+    // x >= thr[d][i]; entries 0 and n are -inf and +inf (not read).
+    const T *thr[3];
+    // 1 when the rounded estimate is itself exact along the axis: lo = 0 and
+    // n / L a power of two, so x - lo and the scaling by n / L are exact in T
+    int est_exact[3];
 };
+
+// Fills thr[0..n] for one axis (host): the smallest T value at or above
+// each face lo + i (hi - lo)/n, each settled by the exact sign of
+// (x - lo) n - i L. Defined in params.cu for T = float and double.
+template <class T> void face_thresholds(double lo, double hi, int n, T *thr);
 
 template <class T> struct Phys {
     T m_g, m_d;
@@ -211,6 +225,8 @@ void make_geo_phys(const tfsph_params &p, const int ncell[3], uint32_t ncells, G
             G.w[d] = T(1);
             G.L[d] = T(1);
             G.halfL[d] = T(0.5);
+            G.thr[d] = nullptr;
+            G.est_exact[d] = 1;
             continue;
         }
         const double L = p.hi[d] - p.lo[d];
@@ -225,6 +241,10 @@ void make_geo_phys(const tfsph_params &p, const int ncell[3], uint32_t ncells, G
         G.w[d] = T(w);
         G.L[d] = T(L);
         G.halfL[d] = T(0.5 * L);
+        G.thr[d] = nullptr;  // set by the owner of the device table
+        int ex = 0;
+        const double mant = frexp((double)n / L, &ex);
+        G.est_exact[d] = (p.lo[d] == 0.0 && mant == 0.5 && (double)T((double)n / L) == (double)n / L) ? 1 : 0;
     }
     G.h2x4 = T(4.0 * p.h * p.h);
     G.lim2 = T(reach * reach * (1.0 + 16.0 * u));
@@ -279,6 +299,9 @@ cudaError_t launch_cell_adjoint(const LaunchCtx &L, const void *geo, const void 
 // ---------------------------------------------------------------------------
 // Device helpers shared by the kernels.
 // ---------------------------------------------------------------------------
+// Rounded cell coordinate t = fl(fl(x - lo) inv) and its floor, clamped to
+// [0, n - 1] (negative or NaN: 0). Places the candidate window of the pair
+// walks, and starts the exact index (exact_cell), within one cell of it.
 template <class T> __device__ __forceinline__ int axis_cell(T x, T lo, T inv, int n, T &t)
 {
     t = mul_rn(sub_rn(x, lo), inv);
@@ -290,13 +313,36 @@ template <class T> __device__ __forceinline__ int axis_cell(T x, T lo, T inv, in
     return i;
 }
 
+// Cell index along axis d, exact: floor((x - lo) n / L) over the reals for
+// the stored coordinate x, lo and L = hi - lo in binary64, clamped to
+// [0, n - 1], NaN to 0 (Sec. 2.3: membership of the disjoint volumes). The
+// rounded estimate is within one cell of it; the face thresholds move it to
+// the exact index (two moves at most either way, whatever happens).
+template <class T> __device__ __forceinline__ int exact_cell(const Geo<T> &G, int d, T x)
+{
+    T t;
+    const int n = G.n[d];
+    int i = axis_cell(x, G.lo[d], G.inv_w[d], n, t);
+    if (G.est_exact[d]) return i;
+    if (!(x == x)) return 0;
+    const T *thr = G.thr[d];
+    if (i > 0 && x < __ldg(&thr[i])) {
+        --i;
+        if (i > 0 && x < __ldg(&thr[i])) --i;
+    } else if (i < n - 1 && !(x < __ldg(&thr[i + 1]))) {
+        ++i;
+        if (i < n - 1 && !(x < __ldg(&thr[i + 1]))) ++i;
+    }
+    return i;
+}
+
+// Cell key, exact per axis; key = ix + nx (iy + ny iz).
 template <class T, int DIM>
 __device__ __forceinline__ uint32_t cell_key(const Geo<T> &G, T x, T y, T z)
 {
-    T t;
-    int ix = axis_cell(x, G.lo[0], G.inv_w[0], G.n[0], t);
-    int iy = DIM > 1 ? axis_cell(y, G.lo[1], G.inv_w[1], G.n[1], t) : 0;
-    int iz = DIM > 2 ? axis_cell(z, G.lo[2], G.inv_w[2], G.n[2], t) : 0;
+    const int ix = exact_cell(G, 0, x);
+    const int iy = DIM > 1 ? exact_cell(G, 1, y) : 0;
+    const int iz = DIM > 2 ? exact_cell(G, 2, z) : 0;
     return (uint32_t)ix + (uint32_t)G.n[0] * ((uint32_t)iy + (uint32_t)G.n[1] * (uint32_t)iz);
 }
 
