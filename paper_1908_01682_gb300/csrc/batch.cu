@@ -336,6 +336,116 @@ template <class T, int DIM, int MODE> __device__ void ph_pair(const BatchArgs<T>
     }
 }
 
+// Tiled gas pair sums of 1D instances (the TFSPH_BATCH_TILED form). The
+// particles of a chunk occupy consecutive cells c_first..c_last, so the
+// candidates of the whole chunk are the particles of the window of cells
+// [c_first - R, c_last + R] (wrapped on a periodic axis): a run of storage,
+// plus across the seam one run at the other end of the instance. The window
+// is staged in shared memory with a local table of cell starts; each thread
+// then walks its particle's candidate cells there, with the arithmetic and
+// the neighbour decision of the global walk. A chunk whose window does not
+// fit (more than kTileCells cells or cap particles), or an instance whose
+// window covers its whole axis, takes the global walk.
+constexpr int kTileCells = 1024;
+
+__host__ __device__ constexpr size_t tile_table_bytes() { return ((kTileCells + 1) * 4 + 15) / 16 * 16; }
+
+template <class T, int MODE>
+__device__ void ph_pair_tiled(const BatchArgs<T> &B, int q, BInst<T> &si, unsigned char *smem, int cap)
+{
+    static_assert(MODE == 0 || MODE == 2, "tiled form: density and isothermal force");
+    int *lst = reinterpret_cast<int *>(smem);
+    V4<T> *sp = reinterpret_cast<V4<T> *>(smem + tile_table_bytes());
+    __shared__ int s_win[2];
+    V4<T> *pos = B.gpos[q];
+    const V4<T> *vel = B.gvel[q];
+    const uint32_t *id = B.gid[q];
+    for (uint32_t c = blockIdx.x; c < B.ngch; c += gridDim.x) {
+        const Chunk ch = B.gch[c];
+        __syncthreads();
+        load_inst(&B.inst[ch.inst], si);
+        __syncthreads();
+        const Geo<T> &G = si.G;
+        const uint32_t *start = B.gstart + si.coff;
+        const int n = G.n[0], R = G.R[0], per = G.per[0];
+        if (threadIdx.x == 0) {
+            const int c0 = (int)cell_key<T, 1>(G, pos[ch.begin].x, T(0), T(0));
+            const int c1 = (int)cell_key<T, 1>(G, pos[ch.end - 1].x, T(0), T(0));
+            s_win[0] = c0 - R;
+            s_win[1] = c1 - c0 + 2 * R + 1;
+        }
+        __syncthreads();
+        const int w0 = s_win[0], nwc = s_win[1];
+        bool tiled = !G.full[0] && nwc <= kTileCells;
+        if (tiled) {
+            // local cell starts of the window (block-wide scan, kTileCells / CTA rounds at most)
+            uint32_t run = 0;
+            for (int h0 = 0; h0 < nwc; h0 += blockDim.x) {
+                const int h = h0 + (int)threadIdx.x;
+                uint32_t cnt = 0;
+                if (h < nwc) {
+                    int gc = w0 + h;
+                    if (per) gc = gc < 0 ? gc + n : (gc >= n ? gc - n : gc);
+                    if (gc >= 0 && gc < n) cnt = start[gc + 1] - start[gc];
+                }
+                uint32_t excl;
+                const uint32_t tot = cta_exclusive_scan(cnt, excl);
+                if (h < nwc) lst[h] = (int)(run + excl);
+                run += tot;
+            }
+            if (threadIdx.x == 0) lst[nwc] = (int)run;
+            tiled = run <= (uint32_t)cap;
+            __syncthreads();
+            if (tiled) {
+                for (int h = threadIdx.x; h < nwc; h += blockDim.x) {
+                    int gc = w0 + h;
+                    if (per) gc = gc < 0 ? gc + n : (gc >= n ? gc - n : gc);
+                    if (gc < 0 || gc >= n) continue;
+                    const uint32_t g0 = start[gc];
+                    for (int j = lst[h]; j < lst[h + 1]; ++j) sp[j] = pos[g0 + (uint32_t)(j - lst[h])];
+                }
+                __syncthreads();
+            }
+        }
+        const uint32_t a = ch.begin + threadIdx.x;
+        if (a < ch.end) {
+            PairAcc<T, MODE> A;
+            const V4<T> pa = pos[a];
+            acc_init(A, si.Ph, pa, vel, B.rho, a);
+            if (tiled) {
+                T t;
+                const int ca = axis_cell(pa.x, G.lo[0], G.inv_w[0], n, t);
+                int olo, ohi;
+                x_window(G, t - T(ca), G.lim2, olo, ohi);
+                const int hl = max(ca + olo - w0, 0), hh = min(ca + ohi - w0, nwc - 1) + 1;  // window cells [hl, hh)
+                // cells h < s0 lie across the low seam, h >= s1 across the high one
+                const int s0 = per ? min(max(-w0, 0), nwc) : 0;
+                const int s1 = per ? max(min(n - w0, nwc), s0) : nwc;
+                auto walk = [&](int h_a, int h_b, auto seam) {
+                    for (int j = lst[h_a]; j < lst[h_b]; ++j) {
+                        const V4<T> pb = sp[j];
+                        T d[3];
+                        const T r2 = pair_r2<T, 1, decltype(seam)::value>(G, pa, pb, d);
+                        A.add(G, si.Ph, pb, nullptr, T(1), 0u, r2, d);
+                    }
+                };
+                // the global walk's order: wrapped from below, wrapped from above, then the rest,
+                // so that both forms sum the same terms in the same order
+                if (hl < min(hh, s0)) walk(hl, min(hh, s0), SeamTag<true>{});
+                if (max(hl, s1) < hh) walk(max(hl, s1), hh, SeamTag<true>{});
+                if (max(hl, s0) < min(hh, s1)) walk(max(hl, s0), min(hh, s1), SeamTag<false>{});
+            } else {
+                walk_global<T, 1, MODE>(A, si.G, si.Ph, pa, pos, vel, B.rho, id, start);
+            }
+            if (MODE == 0)
+                acc_store<T, MODE>(A, si.Ph, a, si.Ph.m_g, vel, B.rho, reinterpret_cast<T *>(pos), nullptr, nullptr,
+                                   nullptr);
+            else
+                acc_store<T, MODE>(A, si.Ph, a, T(0), vel, nullptr, nullptr, B.acc, nullptr, nullptr);
+        }
+    }
+}
+
 // Cell drag and particle update with storage q (the arithmetic of the
 // single context's cell update, per instance); writes the next keys.
 template <class T, class A, int DIM>
@@ -450,6 +560,13 @@ template <int DIM, int MODE> __global__ void __launch_bounds__(kMaxBlock) k_b_pa
 {
     __shared__ BInst<Tf> si;
     ph_pair<Tf, DIM, MODE>(B, ld_parity(B.sp), si);
+}
+
+template <int MODE> __global__ void __launch_bounds__(kMaxBlock) k_b_pair_tiled(BatchArgs<Tf> B, int cap)
+{
+    extern __shared__ __align__(16) unsigned char smem[];
+    __shared__ BInst<Tf> si;
+    ph_pair_tiled<Tf, MODE>(B, ld_parity(B.sp), si, smem, cap);
 }
 
 template <class A, int DIM> __global__ void __launch_bounds__(kMaxBlock, sizeof(A) == 4 ? 3 : 1) k_b_update(BatchArgs<Tf> B)
@@ -708,8 +825,20 @@ template <int DIM> cudaError_t launch_pair_dim(const tfsph_batch *b, const Batch
     return cudaGetLastError();
 }
 
+// Staged particles per chunk of the tiled form: the chunk itself, its
+// window's halo and room for uneven cells.
+int tile_cap(int block) { return 2 * block + 512; }
+size_t tile_smem(int block) { return tile_table_bytes() + (size_t)tile_cap(block) * sizeof(float4); }
+
 cudaError_t launch_pair(const tfsph_batch *b, const BatchArgs<Tf> &B, cudaStream_t s, bool force)
 {
+    if (b->mode == TFSPH_BATCH_TILED && b->dim == 1 && !b->full) {
+        if (B.ngch == 0) return cudaSuccess;
+        const size_t sm = tile_smem(b->block);
+        if (!force) k_b_pair_tiled<0><<<B.ngch, b->block, sm, s>>>(B, tile_cap(b->block));
+        else k_b_pair_tiled<2><<<B.ngch, b->block, sm, s>>>(B, tile_cap(b->block));
+        return cudaGetLastError();
+    }
     switch (b->dim) {
         case 1: return launch_pair_dim<1>(b, B, s, force);
         case 2: return launch_pair_dim<2>(b, B, s, force);
@@ -857,7 +986,10 @@ int run_steps(tfsph_batch *b, int nsteps)
 // (capped by blocks_per_sm per SM).
 int configure(tfsph_batch *b, int mode, int block, int blocks_per_sm, double timeout_ms)
 {
-    if (mode != TFSPH_BATCH_KERNELS && mode != TFSPH_BATCH_PERSISTENT) return bfail(b, TFSPH_E_INVALID_ARG, "unknown batch mode");
+    if (mode != TFSPH_BATCH_KERNELS && mode != TFSPH_BATCH_PERSISTENT && mode != TFSPH_BATCH_TILED)
+        return bfail(b, TFSPH_E_INVALID_ARG, "unknown batch mode");
+    if (mode == TFSPH_BATCH_TILED && (b->dim != 1 || b->full))
+        return bfail(b, TFSPH_E_INVALID_ARG, "the tiled form takes 1D batches of isothermal gas without viscosity");
     if (block != 128 && block != 256 && block != 512) return bfail(b, TFSPH_E_INVALID_ARG, "block must be 128, 256 or 512");
     if (blocks_per_sm < 1 || blocks_per_sm > 16) return bfail(b, TFSPH_E_INVALID_ARG, "blocks_per_sm must be in [1, 16]");
     if (!(timeout_ms >= 0) || !std::isfinite(timeout_ms)) return bfail(b, TFSPH_E_INVALID_ARG, "timeout must be finite and >= 0");
@@ -878,6 +1010,12 @@ int configure(tfsph_batch *b, int mode, int block, int blocks_per_sm, double tim
                                                                  block, update_smem(block)));
         if (occ < 1) return bfail(b, TFSPH_E_INVALID_ARG, "the persistent kernel does not fit an SM at this block size");
         b->grid = std::min(occ, blocks_per_sm) * b->sm_count;
+    }
+    if (mode == TFSPH_BATCH_TILED) {
+        TB_CUDA(b, cudaFuncSetAttribute(k_b_pair_tiled<0>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                        (int)tile_smem(kMaxBlock)));
+        TB_CUDA(b, cudaFuncSetAttribute(k_b_pair_tiled<2>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                        (int)tile_smem(kMaxBlock)));
     }
     return TFSPH_OK;
 }
@@ -1038,6 +1176,26 @@ int tfsph_batch_init(tfsph_batch **out, const tfsph_params *params, const int64_
     const int64_t nmax = std::max<int64_t>(ng, nd);
     b->staging_bytes = (size_t)(2 * p0.dim + 1) * (size_t)nmax * 4 + (size_t)ng + 256;
     if ((rc = balloc(b, &b->staging, b->staging_bytes))) return bail(rc);
+    // exact cell-face thresholds of every instance's axes (cell_key), one table
+    {
+        size_t total = 0;
+        for (int i = 0; i < n_inst; ++i)
+            for (int d = 0; d < p0.dim; ++d) total += (size_t)b->hinst[i].G.n[d] + 1;
+        std::vector<Tf> h(total);
+        std::vector<size_t> off((size_t)n_inst * 3, 0);
+        size_t at = 0;
+        for (int i = 0; i < n_inst; ++i)
+            for (int d = 0; d < p0.dim; ++d) {
+                off[(size_t)i * 3 + d] = at;
+                face_thresholds<Tf>(params[i].lo[d], params[i].hi[d], b->hinst[i].G.n[d], h.data() + at);
+                at += (size_t)b->hinst[i].G.n[d] + 1;
+            }
+        if ((rc = balloc(b, &tmp, total * sizeof(Tf)))) return bail(rc);
+        e = cudaMemcpy(tmp, h.data(), total * sizeof(Tf), cudaMemcpyHostToDevice);
+        if (e != cudaSuccess) return bail(bcuda(b, e, "cudaMemcpy"));
+        for (int i = 0; i < n_inst; ++i)
+            for (int d = 0; d < p0.dim; ++d) b->hinst[i].G.thr[d] = static_cast<const Tf *>(tmp) + off[(size_t)i * 3 + d];
+    }
     e = cudaMemcpy(b->dinst, b->hinst.data(), (size_t)n_inst * sizeof(BInst<Tf>), cudaMemcpyHostToDevice);
     if (e != cudaSuccess) return bail(bcuda(b, e, "cudaMemcpy"));
     if ((rc = configure(b, TFSPH_BATCH_KERNELS, 256, 1, 2000.0))) return bail(rc);
@@ -1160,6 +1318,8 @@ int tfsph_batch_autotune(tfsph_batch *b, int32_t steps, int32_t *mode, int32_t *
     struct Cand { int mode, block, bps; };
     std::vector<Cand> cands;
     for (int blk : {128, 256, 512}) cands.push_back({TFSPH_BATCH_KERNELS, blk, 1});
+    if (b->dim == 1 && !b->full)
+        for (int blk : {128, 256, 512}) cands.push_back({TFSPH_BATCH_TILED, blk, 1});
     for (int blk : {128, 256, 512})
         for (int bps : {1, 2, 4}) cands.push_back({TFSPH_BATCH_PERSISTENT, blk, bps});
     cudaEvent_t e0, e1;

@@ -56,13 +56,15 @@ def _instance_out(bt, b, i, fields):
     return {"gx": f64(gx[:, g0:g1]), "gv": f64(gv[:, g0:g1]), "dx": f64(dx[:, d0:d1]), "du": f64(du[:, d0:d1])}
 
 
-@pytest.mark.parametrize("mode", ["kernels", "persistent"])
+@pytest.mark.parametrize("mode", ["kernels", "persistent", "tiled"])
 def test_batch_1d_matches_oracle_per_instance(orc, mode):
     b = gpu_lib()
     ws = _waves()
     with _batch(b, ws) as bt:
         if mode == "persistent":
             bt.config(b.TFSPH_BATCH_PERSISTENT, 256, 2)
+        elif mode == "tiled":
+            bt.config(b.TFSPH_BATCH_TILED, 128, 1)
         rho = bt.field(b.TFSPH_FIELD_RHO_G)
         bt.step([w.tau for w in ws])
         bt.sync()
@@ -71,6 +73,32 @@ def test_batch_1d_matches_oracle_per_instance(orc, mode):
             gpu = _instance_out(bt, b, i, out)
             gpu["rho_g"] = rho[bt.goff[i]:bt.goff[i + 1]].astype(np.float64)
             check_one_step(orc, w, gpu, 0)
+
+
+@pytest.mark.parametrize("cell_acc", [0, 1])
+def test_batch_ensemble_full_size_matches_oracle(orc, cell_acc):
+    """The benchmarked ensemble, 256 dusty waves of 1k-64k particles (3.9M in
+    total), with FP32 cell sums (cell_acc 0, the benchmarked form) and FP64
+    cell sums, in the launch form the autotuner picks: every instance after
+    one step against the oracle run on that instance alone."""
+    b = gpu_lib()
+    ws = workloads.ensemble1d(precision=0)
+    with _batch(b, ws, cell_acc=cell_acc) as bt:
+        bt.step([w.tau for w in ws], nsteps=0)
+        pick = bt.autotune(steps=3)
+        rho = bt.field(b.TFSPH_FIELD_RHO_G)
+        bt.step(nsteps=1)
+        bt.sync()
+        assert bt.info().steps == 1
+        out = _state(bt, b)
+        worst = {}
+        for i, w in enumerate(ws):
+            gpu = _instance_out(bt, b, i, out)
+            gpu["rho_g"] = rho[bt.goff[i]:bt.goff[i + 1]].astype(np.float64)
+            _, errs = check_one_step(orc, w, gpu, 0)
+            for k, e in errs.items():
+                worst[k] = max(worst.get(k, 0.0), e)
+    print(f"ensemble, cell_acc={cell_acc}, form {pick}: worst errors {worst}")
 
 
 def test_batch_2d_walls_and_gravity_match_oracle(orc):
@@ -86,7 +114,7 @@ def test_batch_2d_walls_and_gravity_match_oracle(orc):
 
 
 @pytest.mark.parametrize("form", [("kernels", 128, 1), ("kernels", 512, 1), ("persistent", 128, 4),
-                                  ("persistent", 512, 1)])
+                                  ("persistent", 512, 1), ("tiled", 128, 1), ("tiled", 256, 1), ("tiled", 512, 1)])
 def test_batch_launch_forms_agree_bit_for_bit(form):
     b = gpu_lib()
     ws = _waves()
@@ -95,7 +123,8 @@ def test_batch_launch_forms_agree_bit_for_bit(form):
         ref.step(taus, nsteps=7)
         want = _state(ref, b)
     with _batch(b, ws) as bt:
-        mode = b.TFSPH_BATCH_PERSISTENT if form[0] == "persistent" else b.TFSPH_BATCH_KERNELS
+        mode = {"persistent": b.TFSPH_BATCH_PERSISTENT, "kernels": b.TFSPH_BATCH_KERNELS,
+                "tiled": b.TFSPH_BATCH_TILED}[form[0]]
         bt.config(mode, form[1], form[2])
         bt.step(taus, nsteps=7)
         bt.sync()
@@ -195,4 +224,15 @@ def test_batch_barrier_timeout_is_reported():
     # a fresh batch on the same device runs normally
     with _batch(b, ws) as bt:
         bt.step([w.tau for w in ws])
+        bt.sync()
+
+
+def test_batch_tiled_form_refused_for_2d():
+    """The tiled form stages windows of consecutive cells: 1D batches only."""
+    b = gpu_lib()
+    with _batch(b, _columns()) as bt:
+        with pytest.raises(b.TfsphError) as ei:
+            bt.config(b.TFSPH_BATCH_TILED, 256, 1)
+        assert ei.value.code == b.TFSPH_E_INVALID_ARG
+        bt.step([w.tau for w in _columns()], g=[(0.0, -1.0)] * 3)  # the batch stays usable
         bt.sync()
