@@ -257,6 +257,41 @@ void tfsph_destroy(tfsph_ctx *c);
 /* Library version, major * 10000 + minor * 100 + patch. */
 int tfsph_version(void);
 
+/* ------------------------------------------------------------------------
+ * Binned dust density and a squared-error loss on it, with the loss's
+ * gradient: the loss of the differentiable rollout (tfsph_step_adjoint). The
+ * paper's test problems compare profiles of the dust density (Sec. 3); this
+ * is the cloud-in-cell form of such a profile.
+ *   grid: nbins[k] bins of width D_k = (hi_k - lo_k)/nbins[k] on each axis
+ *     k < dim (1 <= nbins[k] <= 65536, at most 2^26 bins), bin b = i_0 +
+ *     nbins[0] (i_1 + nbins[1] i_2). A particle at x (s = (x - lo)/D - 1/2,
+ *     i = floor(s), f = s - i per axis) adds mass * prod_k (1 - f_k or f_k)
+ *     to the 2^dim bins (i_k or i_k + 1); periodic axes wrap the bin index,
+ *     other axes clamp it to [0, nbins - 1]; rho_b = deposited mass / bin
+ *     volume. NaN positions are skipped.
+ *   x:      device positions of n particles, component-major (dim, n), of the
+ *           spec's precision (as tfsph_fields exports them).
+ *   rho:    device double[nbins] (caller-owned), the profile.
+ *   target: device double[nbins] or NULL. With a target, loss (device double,
+ *           or NULL) receives sum_b (rho_b - target_b)^2 and lam_x (device,
+ *           (dim, n), spec precision, or NULL) is overwritten with d loss /
+ *           d x (the derivative of the linear piece that holds x).
+ *   stream: cudaStream_t (NULL = legacy default stream); asynchronous.
+ * The deposit accumulates in binary64 with atomics, so the last bits of rho
+ * may depend on the order of the particles' additions.
+ * Errors: INVALID_ARG, CUDA; the message is in tfsph_last_error(NULL). */
+typedef struct {
+    int dim;
+    double lo[3], hi[3];
+    int periodic[3];
+    int nbins[3];
+    double mass;      /* mass of every particle */
+    int precision;    /* TFSPH_FP32 or TFSPH_FP64: the type of x and lam_x */
+} tfsph_grid_spec;
+
+int tfsph_dust_profile(const tfsph_grid_spec *grid, const void *x, int64_t n, const void *target, void *rho,
+                       void *loss, void *lam_x, void *stream);
+
 /* Cell ranges of a set of cell keys, computed without allocating any device
  * memory. The paper has no counterpart: this is an entry point for callers
  * that cannot call cudaMalloc, such as applications whose device memory is
@@ -275,8 +310,11 @@ int tfsph_version(void);
  * device current); make that first call before any stream capture. All calls
  * on a device share that device's array and each clears the counters it
  * uses first, so calls that overlap on the same GPU (on different streams)
- * race: order them on one stream. Errors: INVALID_ARG, CUDA; the message is
- * in tfsph_last_error(NULL). */
+ * race: order them on one stream. The device address is kept for the life
+ * of the process: calls after cudaDeviceReset are not supported. A CUDA
+ * error already pending when the call starts is returned as CUDA and left
+ * pending. Errors: INVALID_ARG, CUDA; the message is in
+ * tfsph_last_error(NULL). */
 int tfsph_cell_ranges_noalloc(const uint32_t *keys, int64_t n, uint32_t n_cells, uint32_t *starts,
                               void *stream);
 
@@ -295,7 +333,14 @@ int tfsph_cell_ranges_noalloc(const uint32_t *keys, int64_t n, uint32_t n_cells,
  *     separated by grid barriers whose waits are bounded (a wait that runs
  *     out makes the next tfsph_batch_sync return TFSPH_E_TIMEOUT; the
  *     context stays usable);
- *   TFSPH_BATCH_KERNELS: one launch per phase (the default).
+ *   TFSPH_BATCH_KERNELS: one launch per phase (the default); the gas pair
+ *     sums walk each particle's candidate cells in global memory;
+ *   TFSPH_BATCH_TILED: one launch per phase, and the gas pair sums stage the
+ *     candidate cells of each chunk of CTA-size particles (a window of
+ *     consecutive cells) in shared memory. 1D batches of isothermal gas
+ *     without viscosity only (INVALID_ARG otherwise).
+ * The CTA size (128, 256 or 512) is also the tile of the tiled form: the
+ * number of consecutive particles whose window is staged together.
  * tfsph_batch_autotune times the forms and CTA sizes on the current state
  * (which it restores) and keeps the fastest.
  * ---------------------------------------------------------------------- */
@@ -303,6 +348,7 @@ typedef struct tfsph_batch tfsph_batch;
 
 #define TFSPH_BATCH_KERNELS    0
 #define TFSPH_BATCH_PERSISTENT 1
+#define TFSPH_BATCH_TILED      2
 
 typedef struct {
     int32_t n_inst, dim;

@@ -11,8 +11,10 @@ adjoint after the snapshot is loaded.
 
 ``TFSPHRollout`` wraps it in a ``torch.autograd.Function``: gradients of any
 loss on the final state with respect to the per-particle stopping times and
-the initial gas and dust velocities. All work is done by the CUDA library;
-torch provides device tensors.
+the initial gas and dust velocities. ``DustProfileLoss`` is such a loss: the
+squared error of the binned (cloud-in-cell) dust density against a target
+profile, evaluated with its gradient by ``tfsph_dust_profile``. All work is
+done by the CUDA library; torch provides device tensors.
 """
 from __future__ import annotations
 
@@ -104,3 +106,47 @@ class TFSPHRollout(torch.autograd.Function):
         lgx, lgv, ldx, ldu = z(ref[0], lgx), z(ref[1], lgv), z(ref[2], ldx), z(ref[3], ldu)
         l0 = r.backward(lgx, lgv, ldx, ldu)
         return l0[4], l0[1], l0[3], None, None, None
+
+
+def profile_grid(ctx: "b.Context", nbins) -> "b.tfsph_grid_spec":
+    """Grid spec of a context's box for the dust profile (nbins per axis)."""
+    p = ctx.params
+    return b.grid_spec(p.dim, list(p.lo), list(p.hi), list(p.periodic), nbins, p.m_dust, p.precision)
+
+
+def dust_profile(grid: "b.tfsph_grid_spec", dx: torch.Tensor) -> torch.Tensor:
+    """Binned dust density (float64, bins with axis 0 fastest) of positions dx (dim, n)."""
+    nb = 1
+    for k in range(grid.dim):
+        nb *= grid.nbins[k]
+    rho = torch.empty(nb, dtype=torch.float64, device=dx.device)
+    x = dx.detach().contiguous()
+    rc = b.tfsph_dust_profile(grid, x.data_ptr(), x.shape[1], None, rho.data_ptr(), None, None,
+                              torch.cuda.current_stream().cuda_stream)
+    if rc != b.TFSPH_OK:
+        raise b.TfsphError(rc, b.tfsph_last_error(None))
+    return rho
+
+
+class DustProfileLoss(torch.autograd.Function):
+    """loss = sum_b (rho_b(dx) - target_b)^2 for the binned dust density of
+    positions dx (dim, n); the library returns d loss / d dx with the loss."""
+
+    @staticmethod
+    def forward(fctx, dx, target, grid):
+        x = dx.detach().contiguous()
+        t = target.detach().to(torch.float64).contiguous()
+        rho = torch.empty_like(t)
+        loss = torch.empty(1, dtype=torch.float64, device=x.device)
+        lam = torch.empty_like(x)
+        rc = b.tfsph_dust_profile(grid, x.data_ptr(), x.shape[1], t.data_ptr(), rho.data_ptr(), loss.data_ptr(),
+                                  lam.data_ptr(), torch.cuda.current_stream().cuda_stream)
+        if rc != b.TFSPH_OK:
+            raise b.TfsphError(rc, b.tfsph_last_error(None))
+        fctx.save_for_backward(lam)
+        return loss[0]
+
+    @staticmethod
+    def backward(fctx, gl):
+        (lam,) = fctx.saved_tensors
+        return lam * gl.to(lam.dtype), None, None

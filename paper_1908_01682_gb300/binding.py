@@ -21,7 +21,7 @@ LIB_PATH = os.path.join(_HERE, "libtfsph.so")
 # constants mirrored from include/tfsph.h
 TFSPH_OK, TFSPH_E_INVALID_ARG, TFSPH_E_NONFINITE, TFSPH_E_OUT_OF_DOMAIN = 0, 1, 2, 3
 TFSPH_E_CUDA, TFSPH_E_OOM, TFSPH_E_INTERNAL, TFSPH_E_TIMEOUT = 4, 5, 6, 7
-TFSPH_BATCH_KERNELS, TFSPH_BATCH_PERSISTENT = 0, 1
+TFSPH_BATCH_KERNELS, TFSPH_BATCH_PERSISTENT, TFSPH_BATCH_TILED = 0, 1, 2
 TFSPH_MEM_HOST, TFSPH_MEM_DEVICE = 0, 1
 TFSPH_FP32, TFSPH_FP64 = 0, 1
 TFSPH_EOS_ISOTHERMAL, TFSPH_EOS_ADIABATIC = 0, 1
@@ -63,6 +63,24 @@ class tfsph_batch_info_t(C.Structure):
         ("n_cells", C.c_int64), ("mode", C.c_int32), ("block", C.c_int32), ("grid", C.c_int32),
         ("graph", C.c_int32), ("steps", C.c_int64), ("launches", C.c_int64), ("device_bytes", C.c_int64),
     ]
+
+
+class tfsph_grid_spec(C.Structure):
+    _fields_ = [
+        ("dim", C.c_int32), ("lo", C.c_double * 3), ("hi", C.c_double * 3), ("periodic", C.c_int32 * 3),
+        ("nbins", C.c_int32 * 3), ("mass", C.c_double), ("precision", C.c_int32),
+    ]
+
+
+def grid_spec(dim, lo, hi, periodic, nbins, mass, precision) -> tfsph_grid_spec:
+    g = tfsph_grid_spec()
+    g.dim, g.mass, g.precision = int(dim), float(mass), int(precision)
+    for k in range(3):
+        g.lo[k] = float(lo[k]) if k < len(lo) else 0.0
+        g.hi[k] = float(hi[k]) if k < len(hi) else 1.0
+        g.periodic[k] = int(periodic[k]) if k < len(periodic) else 0
+        g.nbins[k] = int(nbins[k]) if k < len(nbins) else 1
+    return g
 
 
 class TfsphError(RuntimeError):
@@ -108,6 +126,7 @@ def load() -> C.CDLL:
     lib.tfsph_profile.argtypes = [ctxp, i32]
     lib.tfsph_cell_ranges_noalloc.argtypes = [vp, i64, C.c_uint32, vp, vp]
     lib.tfsph_profile_read.argtypes = [ctxp, vp, vp, vp]
+    lib.tfsph_dust_profile.argtypes = [C.POINTER(tfsph_grid_spec), vp, i64, vp, vp, vp, vp, vp]
     lib.tfsph_last_error.argtypes = [ctxp]
     lib.tfsph_last_error.restype = C.c_char_p
     lib.tfsph_status_string.argtypes = [i32]
@@ -134,7 +153,7 @@ def load() -> C.CDLL:
     for name in ("tfsph_init", "tfsph_set_state", "tfsph_set_stream", "tfsph_step", "tfsph_step_adjoint", "tfsph_max_dt",
                  "tfsph_fields", "tfsph_debug", "tfsph_info", "tfsph_sync", "tfsph_version",
                  "tfsph_profile", "tfsph_profile_read", "tfsph_cell_ranges_noalloc", "tfsph_state_bytes",
-                 "tfsph_save_state", "tfsph_load_state"):
+                 "tfsph_save_state", "tfsph_load_state", "tfsph_dust_profile"):
         getattr(lib, name).restype = C.c_int
     _lib = lib
     return lib
@@ -186,6 +205,12 @@ def tfsph_save_state(ctx, buf_ptr, mem_kind: int) -> int:
 
 def tfsph_load_state(ctx, buf_ptr, mem_kind: int) -> int:
     return load().tfsph_load_state(ctx, buf_ptr, int(mem_kind))
+
+
+def tfsph_dust_profile(grid: tfsph_grid_spec, x_ptr, n: int, target_ptr, rho_ptr, loss_ptr, lam_x_ptr,
+                       stream_ptr) -> int:
+    return load().tfsph_dust_profile(C.byref(grid), x_ptr, int(n), target_ptr, rho_ptr, loss_ptr, lam_x_ptr,
+                                     stream_ptr)
 
 
 def tfsph_max_dt(ctx, cfl: float):
