@@ -127,8 +127,13 @@ extern "C" int tfsph_cell_ranges_noalloc(const uint32_t *keys, int64_t n, uint32
         return noalloc_fail(TFSPH_E_INVALID_ARG, "n_cells must be in [1, 2097152] (the static scratch holds 2^21 cell counters)");
     if (n < 0 || n >= ((int64_t)1 << 31)) return noalloc_fail(TFSPH_E_INVALID_ARG, "n must be in [0, 2^31)");
     if (!starts || (n > 0 && !keys)) return noalloc_fail(TFSPH_E_INVALID_ARG, "NULL keys or starts");
+    // an error left by an earlier, unrelated call stays the caller's: report
+    // it without clearing it, so the status below only ever describes this
+    // call's own launches
+    cudaError_t e = cudaPeekAtLastError();
+    if (e != cudaSuccess) return noalloc_fail(TFSPH_E_CUDA, "a CUDA error from an earlier call is pending");
     int dev = -1;
-    cudaError_t e = cudaGetDevice(&dev);
+    e = cudaGetDevice(&dev);
     if (e != cudaSuccess) return noalloc_fail(TFSPH_E_CUDA, cudaGetErrorString(e));
     if (dev < 0 || dev >= kMaxDevices) return noalloc_fail(TFSPH_E_INVALID_ARG, "device ordinal out of range");
     uint32_t *scratch;

@@ -16,7 +16,8 @@ pytestmark = pytest.mark.gpu
 
 
 def _ranges_noalloc(b, torch, keys, n_cells):
-    d_keys = torch.tensor(keys.astype(np.int64), dtype=torch.int64, device="cuda").to(torch.int32)
+    # the uint32 key bits, carried by an int32 tensor
+    d_keys = torch.from_numpy(np.ascontiguousarray(keys.astype(np.uint32).view(np.int32))).to("cuda")
     d_starts = torch.full((n_cells + 1,), -1, dtype=torch.int32, device="cuda")
     stream = torch.cuda.current_stream()
     rc = b.tfsph_cell_ranges_noalloc(d_keys.data_ptr(), keys.size, n_cells, d_starts.data_ptr(),
@@ -52,3 +53,25 @@ def test_cell_ranges_noalloc_rejects_too_many_cells():
     rc = b.tfsph_cell_ranges_noalloc(keys.data_ptr(), 4, (1 << 21) + 1, starts.data_ptr(), None)
     assert rc == b.TFSPH_E_INVALID_ARG
     assert "2097152" in b.tfsph_last_error(None)
+
+
+def test_cell_ranges_noalloc_large_grids_and_keys_out_of_range():
+    """Grids of 2^21 cells (the largest accepted: 1024 scan blocks, so the
+    carry loop of the block-total scan runs several passes) and of 2^19 + 3
+    cells (a partial last scan block), with seeded random keys of which some
+    lie beyond the grid (up to 0xFFFFFFFF): the starts equal the prefix sums
+    of the in-range key counts, bit for bit, on two calls in a row."""
+    torch = pytest.importorskip("torch")
+    b = gpu_lib()
+    rng = np.random.default_rng(41)
+    for n_cells in ((1 << 21), (1 << 19) + 3):
+        keys = rng.integers(0, n_cells, size=300_000, dtype=np.int64)
+        out = rng.choice(keys.size, size=1000, replace=False)
+        keys[out] = rng.integers(n_cells, 1 << 32, size=out.size, dtype=np.int64)
+        keys[out[:10]] = 0xFFFFFFFF
+        keys[out[10:20]] = n_cells
+        inside = keys[keys < n_cells]
+        ref = np.concatenate([[0], np.cumsum(np.bincount(inside, minlength=n_cells))])
+        for _ in range(2):
+            got = _ranges_noalloc(b, torch, keys, n_cells)
+            assert np.array_equal(got, ref)
