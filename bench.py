@@ -208,6 +208,16 @@ def algorithmic(phase: str, w, info, nb_mean: float) -> tuple[str, float]:
     raise ValueError(phase)
 
 
+def step_model_bytes(w, info) -> float:
+    """Algorithmic bytes of one step (FP32 state): sort 16 B, gather 56 B (gas)
+    or 64 B (dust), density 16 B (gas), force + drag + update + next key 56 B
+    per particle-update, plus the cell ranges of both phases (start and end,
+    4 B each, per cell). Each of the step's three global dependencies (binning
+    -> density -> force and drag) costs one round trip through HBM; reuse of
+    neighbour data from shared memory or L2 is not counted."""
+    return 144.0 * w.n_gas + 136.0 * w.n_dust + 2 * 2 * 4.0 * info.n_cells_total
+
+
 def peaks():
     path = os.path.join(ROOT, "MEASURED_PEAKS.json")
     try:
@@ -271,21 +281,67 @@ def oracle_sample(workload: str, scale: int):
     p = oracle.Params(dim=q["dim"], lo=q["lo"], hi=q["hi"], periodic=q["periodic"], h=q["h"],
                       cell_size=q["cell_size"], m_gas=q["m_gas"], m_dust=q["m_dust"], eos=q["eos"],
                       cs=q["cs"], gamma=q["gamma"], av_alpha=q["av_alpha"], av_beta=q["av_beta"],
-                      tstar_mode=q["tstar_mode"], decide_fp32=1)
+                      tstar_mode=q["tstar_mode"], path_fp32=1)
     s = oracle.make_state(p, w.gx, w.gv, w.dx, w.du, w.tstop, ge=w.ge, frozen=w.frozen)
     return oracle, p, s, w, desc
 
 
-def cpu_baseline(workload: str, scale: int, steps: int = 1) -> dict:
+def cpu_baseline(workload: str, scale: int, single_scale: int) -> tuple[dict, tuple]:
+    """The oracle timed on all host cores (one step of the workload itself)
+    and on one core (one step of a smaller sample of the same workload).
+    Also returns the all-core step's inputs and results, for the per-field
+    errors of the GPU step."""
     oracle, p, s, w, desc = oracle_sample(workload, scale)
     oracle.build()
+    cores = oracle.set_threads(oracle.omp_threads())
     t0 = time.perf_counter()
-    for _ in range(steps):
-        oracle.step(p, s, w.tau, w.g)
+    r = oracle.step(p, s, w.tau, w.g)
     dt = time.perf_counter() - t0
     n = w.n_gas + w.n_dust
-    return {"value": n * steps / dt, "unit": UNIT, "cores": oracle.omp_threads(), "kind": "oracle",
-            "sample": f"{steps} FP64 oracle step(s) of {desc} ({n} particles), {dt:.2f} s wall"}
+    out = {"value": n / dt, "unit": UNIT, "cores": cores, "kind": "oracle",
+           "sample": f"1 FP64 oracle step of {desc} ({n} particles), {dt:.2f} s wall, {cores} threads"}
+    _, p1, s1, w1, desc1 = oracle_sample(workload, single_scale)
+    oracle.set_threads(1)
+    t0 = time.perf_counter()
+    oracle.step(p1, s1, w1.tau, w1.g)
+    dt1 = time.perf_counter() - t0
+    oracle.set_threads(cores)
+    n1 = w1.n_gas + w1.n_dust
+    out["single_thread"] = {"value": n1 / dt1, "unit": UNIT, "cores": 1,
+                            "sample": f"1 FP64 oracle step of {desc1} ({n1} particles), {dt1:.2f} s wall"}
+    return out, (oracle, p, s, r, w)
+
+
+def field_errors(b, ctx_params, orc_run) -> dict:
+    """Normwise error, ||x - x_ref|| / ||x_ref||, of every field of one GPU
+    step of the workload against the oracle's step from the same inputs
+    (densities before the step; positions as minimum images on periodic axes)."""
+    import numpy as np
+
+    oracle, p, s, r, w = orc_run
+    f32 = lambda a: None if a is None else np.ascontiguousarray(a, dtype=np.float32)
+    with b.Context(ctx_params, f32(w.gx), f32(w.gv), f32(w.dx), f32(w.du), f32(w.tstop), ge=f32(w.ge),
+                   frozen=w.frozen) as c:
+        rho_g = c.field(b.TFSPH_FIELD_RHO_G).astype(np.float64)
+        rho_d = c.field(b.TFSPH_FIELD_RHO_D).astype(np.float64)
+        c.step(w.tau, w.g)
+        got = {k: c.field(f).astype(np.float64) for k, f in
+               (("x_g", b.TFSPH_FIELD_POS_G), ("v_g", b.TFSPH_FIELD_VEL_G), ("x_d", b.TFSPH_FIELD_POS_D),
+                ("u_d", b.TFSPH_FIELD_VEL_D))}
+    ref_rho_d = oracle.density(p, w.dx, p.m_dust)[0]
+
+    def nw(a, ref, pos=False):
+        d = np.asarray(a, np.float64) - np.asarray(ref, np.float64)
+        if pos:
+            for k in range(w.dim):
+                if w.params["periodic"][k]:
+                    L = w.params["hi"][k] - w.params["lo"][k]
+                    d[k] -= L * np.round(d[k] / L)
+        return float(np.linalg.norm(d) / max(np.linalg.norm(ref), 1e-300))
+
+    return {"rho_g": nw(rho_g, r.rho_g), "rho_d": nw(rho_d, ref_rho_d), "x_g": nw(got["x_g"], s.gx, True),
+            "v_g": nw(got["v_g"], s.gv), "x_d": nw(got["x_d"], s.dx, True), "u_d": nw(got["u_d"], s.du),
+            "metric": "normwise ||gpu - oracle|| / ||oracle|| after one step from the workload's inputs"}
 
 
 def run_reference(args, dist: Dist):
@@ -405,14 +461,39 @@ def run_ours(args, dist: Dist):
         achieved = amount / (phase_avg[dominant] * 1e-3) / 1e12
         peak = fp32_alu_peak_tflops(sm_count, mhz)
         unit = "TFLOP/s"
-    step_bytes = sum(algorithmic(ph, w, info, nb_mean)[1] for ph in ("count", "scan", "scatter", "gather", "drag")) \
-        + (24.0 + 32.0) * w.n_gas
+    step_bytes = step_model_bytes(w, info)
     roof = {"kernel": dominant, "bound": bound, "achieved": achieved, "peak": peak, "unit": unit,
             "frac": achieved / peak, "traffic": recorded_traffic(args.workload, dominant),
             "peak_source": pk_src if bound == "hbm" else
             f"derived: 128 FP32 FMA lanes x 2 flops x {sm_count} SMs x {mhz:.0f} MHz ({mhz_src})",
             "step_hbm_frac": (step_bytes / (ms_per_step * 1e-3) / 1e9) / float(pk.get("hbm_gbs", 6800.0)),
-            "step_algorithmic_bytes": step_bytes}
+            "step_algorithmic_bytes": step_bytes,
+            "step_model": "144 B per gas + 136 B per dust particle-update + 2 phases x 2 x 4 B per cell"}
+
+    # ---- the same run with FP64 cell sums and drag factors (the precision mode
+    # that keeps the stiff limit); the headline above uses the FP32 cell sums
+    # of this workload's configuration ----
+    cells_fp64 = None
+    if cell_acc == b.TFSPH_CELL_ACC_FP32:
+        p64 = b.params_from_dict(w.params, cell_acc=b.TFSPH_CELL_ACC_FP64)
+        with b.Context(p64, f32(w.gx), f32(w.gv), f32(w.dx), f32(w.du), f32(w.tstop), ge=f32(w.ge),
+                       frozen=w.frozen) as c64:
+            c64.set_stream(stream)
+            for _ in range(args.warmup):
+                c64.step(w.tau, w.g)
+            torch.cuda.synchronize()
+            e0.record(stream)
+            for _ in range(args.steps):
+                c64.step(w.tau, w.g)
+            e1.record(stream)
+            torch.cuda.synchronize()
+            c64.profile(True)
+            for _ in range(min(args.steps, 10)):
+                c64.step(w.tau, w.g)
+            pm, ps, _ = c64.profile_read()
+        cells_fp64 = {"ms_per_step": e0.elapsed_time(e1) / args.steps,
+                      "drag_ms": pm.get("drag", 0.0) / max(1, ps),
+                      "note": "same steps with FP64 cell sums, slip and drag factors (cell_acc FP64)"}
 
     # ---- end to end through the C ABI with host buffers ----
     e2e = None
@@ -432,8 +513,12 @@ def run_ours(args, dist: Dist):
         schemes = run_schemes(b, args)
 
     cpu = None
+    errors = None
     if dist.rank == 0 and dist.world == 1 and not args.no_cpu_baseline:
-        cpu = cpu_baseline(args.workload, 0)
+        single = {"box3d": 48, "dustyshock": 40000, "column2d": 128}[args.workload]
+        cpu, orc_run = cpu_baseline(args.workload, 0, single)
+        errors = field_errors(b, p, orc_run)
+        del orc_run
 
     ctx.close()
     line = {
@@ -446,19 +531,25 @@ def run_ours(args, dist: Dist):
         "clocks": clk, "e2e": e2e, "gpu_launches": int(launches),
         "roofline": roof,
         "kernel_ms": {k: round(v, 5) for k, v in phase_avg.items()},
+        "cell_sums_fp64": cells_fp64,
         "adjoint": adj,
         "batched": batch,
         "drag_schemes": schemes,
         "cpu_baseline": cpu,
+        "errors": errors,
     }
     if dist.rank == 0:
         print(json.dumps(line), flush=True)
 
 
 def run_adjoint(b, args):
-    """Adjoint cost: a checkpointed rollout on the 2D settling column (512^2 +
-    512^2, FP32) - forward of K steps vs the backward (segment recompute +
-    step adjoints), both through the library, wall time with synchronisation."""
+    """Adjoint cost on the settling column (512^2 gas + 512^2 dust, FP32):
+    loss = squared error of the final binned dust density (64 x 64 bins,
+    cloud in cell) against a seeded target profile after 500 steps
+    checkpointed every 50, gradients with respect to the per-particle t_stop
+    and the initial velocities. Forward = the rollout with its checkpoints and
+    the loss; backward = the loss gradient, the per-segment recompute and the
+    step adjoints. CUDA events on the library's stream around each."""
     import numpy as np
     import torch
 
@@ -467,33 +558,46 @@ def run_adjoint(b, args):
     w, desc = make_workload("column2d")
     p = b.params_from_dict(w.params)
     f32 = lambda a: np.ascontiguousarray(a, dtype=np.float32)
-    nsteps, every = 20, 10
+    nsteps, every, nb = 500, 50, (64, 64)
+    stream = torch.cuda.current_stream()
+    e0, e1, e2 = (torch.cuda.Event(enable_timing=True) for _ in range(3))
     with b.Context(p, f32(w.gx), f32(w.gv), f32(w.dx), f32(w.du), f32(w.tstop), frozen=w.frozen) as c:
-        c.set_stream(torch.cuda.current_stream())
+        c.set_stream(stream)
         dev = lambda a: torch.tensor(f32(a), device="cuda")
-        st0 = (dev(w.gx), dev(w.gv), dev(w.dx), dev(w.du), dev(w.tstop))
+        grid = adjoint.profile_grid(c, nb)
+        rho0 = adjoint.dust_profile(grid, dev(w.dx))
+        rng = np.random.default_rng(8)
+        target = rho0 * torch.tensor(1.0 + 0.1 * rng.standard_normal(rho0.numel()), device="cuda")
         roll = adjoint.Rollout(c, w.tau, w.g, nsteps, checkpoint_every=every, frozen=w.frozen)
-        # warm-up of both directions
-        roll.forward(st0)
-        lam = [torch.ones_like(t) for t in st0[:4]]
-        roll.backward(*lam)
-        torch.cuda.synchronize()
-        roll.restore(st0)
-        torch.cuda.synchronize()
-        t0 = time.perf_counter()
-        for _ in range(nsteps):
-            c.step(w.tau, w.g)
-        torch.cuda.synchronize()
-        fwd = time.perf_counter() - t0
-        roll.forward(st0)
-        torch.cuda.synchronize()
-        t0 = time.perf_counter()
-        roll.backward(*lam)
-        torch.cuda.synchronize()
-        bwd = time.perf_counter() - t0
-    return {"workload": desc, "steps": nsteps, "checkpoint_every": every, "forward_ms": fwd * 1e3,
-            "backward_ms": bwd * 1e3, "ratio": bwd / fwd,
-            "note": "backward = per-segment recompute + state restores + step adjoints"}
+
+        def forward_backward(timed):
+            ts = dev(w.tstop).requires_grad_()
+            gv0 = dev(w.gv).requires_grad_()
+            du0 = dev(w.du).requires_grad_()
+            gx0, dx0 = dev(w.gx), dev(w.dx)
+            torch.cuda.synchronize()
+            if timed:
+                e0.record(stream)
+            _, _, dxf, _ = adjoint.TFSPHRollout.apply(ts, gv0, du0, roll, gx0, dx0)
+            loss = adjoint.DustProfileLoss.apply(dxf, target, grid)
+            if timed:
+                e1.record(stream)
+            loss.backward()
+            if timed:
+                e2.record(stream)
+            torch.cuda.synchronize()
+            return float(loss), ts.grad, gv0.grad, du0.grad
+
+        forward_backward(False)  # warm-up of both directions (allocates the snapshot buffers)
+        loss, gts, ggv, gdu = forward_backward(True)
+        fwd, bwd = e0.elapsed_time(e1), e1.elapsed_time(e2)
+        finite = bool(torch.isfinite(gts).all() and torch.isfinite(ggv).all() and torch.isfinite(gdu).all())
+    return {"workload": desc, "steps": nsteps, "checkpoint_every": every,
+            "loss": "squared error of the 64 x 64 cloud-in-cell dust density after the rollout vs a seeded target",
+            "gradients": "d loss / d t_stop (per particle), d loss / d initial gas and dust velocities",
+            "forward_ms": fwd, "backward_ms": bwd, "ratio": bwd / fwd, "loss_value": loss,
+            "gradients_finite": finite,
+            "timing": "CUDA events on the library's stream; forward includes the checkpoints and the loss"}
 
 
 def run_batch(b, args):
@@ -529,6 +633,18 @@ def run_batch(b, args):
 
     items = [(b.params_from_dict(w.params, cell_acc=cell_acc), w.gx, w.gv, w.dx, w.du, w.tstop) for w in ws]
     bsteps, lsteps = 100, 10
+    forms = {}
+    with b.Batch(items, stream=stream) as bt:
+        bt.step(taus, nsteps=0)
+        # every launch form at 256 threads, timed from the same state (the
+        # autotuner below restores the state it found)
+        for name, mode, bps in (("kernels", b.TFSPH_BATCH_KERNELS, 1), ("tiled", b.TFSPH_BATCH_TILED, 1),
+                                ("persistent", b.TFSPH_BATCH_PERSISTENT, 4)):
+            bt.config(mode, 256, bps)
+            bt.step(nsteps=2)
+            forms[name] = timed(lambda k: bt.step(nsteps=k), 10)
+        bt.sync()
+        bt.close()
     with b.Batch(items, stream=stream) as bt:
         bt.step(taus, nsteps=0)
         pick = bt.autotune(steps=10)
@@ -558,16 +674,20 @@ def run_batch(b, args):
         for c in ctxs:
             c.close()
     wsum = types.SimpleNamespace(n_gas=ng, n_dust=nd)
-    step_bytes = sum(algorithmic(ph, wsum, types.SimpleNamespace(n_cells_total=ncells), 0.0)[1]
-                     for ph in ("count", "scan", "scatter", "gather", "drag")) + (24.0 + 32.0) * ng
+    step_bytes = step_model_bytes(wsum, types.SimpleNamespace(n_cells_total=ncells))
     pk, pk_src = peaks()
     hbm = float(pk.get("hbm_gbs", 6800.0))
     return {
         "workload": f"{len(ws)} independent 1D periodic dusty waves, 1k-64k particles each (log-uniform), "
                     f"t_stop log-uniform 1e-5..1, amplitudes 1e-5..1e-3, h=1.2dx, cell 2h, FP32",
         "instances": len(ws), "particles": n, "cells": ncells,
-        "form": {"mode": "persistent" if pick["mode"] == b.TFSPH_BATCH_PERSISTENT else "kernels",
-                 "block": pick["block"], "blocks_per_sm": pick["blocks_per_sm"], "graph": bool(info.graph)},
+        "form": {"mode": {b.TFSPH_BATCH_PERSISTENT: "persistent", b.TFSPH_BATCH_TILED: "tiled"}.get(
+                     pick["mode"], "kernels"),
+                 "block": pick["block"], "blocks_per_sm": pick["blocks_per_sm"], "graph": bool(info.graph),
+                 "tile": (f"{pick['block']} consecutive particles per CTA, their cells +- R staged in shared memory"
+                          if pick["mode"] == b.TFSPH_BATCH_TILED else "none (global-memory walk)"),
+                 "picked_by": "tfsph_batch_autotune over forms x CTA sizes (x CTAs per SM, persistent)"},
+        "forms_ms_per_step_at_256_threads": forms,
         "batched_ms_per_step": batched_ms, "looped_ms_per_step": looped_ms,
         "speedup_vs_looped": looped_ms / batched_ms,
         "value": n / (batched_ms * 1e-3), "unit": UNIT,
