@@ -53,6 +53,7 @@ def parse_args(argv=None):
     ap.add_argument("--no-adjoint", action="store_true")
     ap.add_argument("--no-batch", action="store_true")
     ap.add_argument("--no-schemes", action="store_true")
+    ap.add_argument("--no-fp64-cells", action="store_true")
     return ap.parse_args(argv)
 
 
@@ -474,7 +475,7 @@ def run_ours(args, dist: Dist):
     # that keeps the stiff limit); the headline above uses the FP32 cell sums
     # of this workload's configuration ----
     cells_fp64 = None
-    if cell_acc == b.TFSPH_CELL_ACC_FP32:
+    if cell_acc == b.TFSPH_CELL_ACC_FP32 and not args.no_fp64_cells:
         p64 = b.params_from_dict(w.params, cell_acc=b.TFSPH_CELL_ACC_FP64)
         with b.Context(p64, f32(w.gx), f32(w.gv), f32(w.dx), f32(w.du), f32(w.tstop), ge=f32(w.ge),
                        frozen=w.frozen) as c64:

@@ -25,7 +25,7 @@
 namespace tfsph {
 namespace {
 
-template <class T, class A, int DIM>
+template <class T, class A, int DIM, bool EST>
 __global__ void __launch_bounds__(kCellsPerCta, (sizeof(T) == 4 && sizeof(A) == 4) ? 12 : 1)
 k_cell_update(Geo<T> G, Phys<T> Ph, A tau, A g0, A g1, A g2, int harmonic, int has_frozen, int adiabatic,
               V4<T> *__restrict__ gpos, V4<T> *__restrict__ gvel, const uint32_t *__restrict__ gid,
@@ -72,12 +72,12 @@ k_cell_update(Geo<T> G, Phys<T> Ph, A tau, A g0, A g1, A g2, int harmonic, int h
         for (uint32_t a = a0 + threadIdx.x; a < a1; a += blockDim.x) {
             V4<T> p = gpos[a];
             if (has_frozen && (gid[a] & kFrozenBit)) {
-                gkey[a] = cell_key<T, DIM>(G, p.x, p.y, p.z);
+                gkey[a] = cell_key<T, DIM, EST>(G, p.x, p.y, p.z);
                 continue;
             }
             V4<T> v = gvel[a];
             const V4<T> ac = acc[a];
-            const uint32_t lc = cell_key<T, DIM>(G, p.x, p.y, p.z) - c0;
+            const uint32_t lc = cell_key<T, DIM, EST>(G, p.x, p.y, p.z) - c0;
             const bool dr = lc < (uint32_t)kCellsPerCta && s_drag[lc];
             T us[3] = {T(0), T(0), T(0)}, ig = T(0);
             if (dr) {
@@ -88,7 +88,7 @@ k_cell_update(Geo<T> G, Phys<T> Ph, A tau, A g0, A g1, A g2, int harmonic, int h
             gas_particle_update<T, DIM>(G, tau_t, gt, adiabatic, p, v, ac, dr, us, ig);
             gpos[a] = p;
             gvel[a] = v;
-            gkey[a] = cell_key<T, DIM>(G, p.x, p.y, p.z);
+            gkey[a] = cell_key<T, DIM, EST>(G, p.x, p.y, p.z);
         }
     }
     {
@@ -96,7 +96,7 @@ k_cell_update(Geo<T> G, Phys<T> Ph, A tau, A g0, A g1, A g2, int harmonic, int h
         for (uint32_t j = j0 + threadIdx.x; j < j1; j += blockDim.x) {
             V4<T> p = dpos[j];
             V4<T> u = dvel[j];
-            const uint32_t lc = cell_key<T, DIM>(G, p.x, p.y, p.z) - c0;
+            const uint32_t lc = cell_key<T, DIM, EST>(G, p.x, p.y, p.z) - c0;
             const bool dr = lc < (uint32_t)kCellsPerCta && s_drag[lc];
             T vs[3] = {T(0), T(0), T(0)}, id = T(0);
             if (dr) {
@@ -107,7 +107,7 @@ k_cell_update(Geo<T> G, Phys<T> Ph, A tau, A g0, A g1, A g2, int harmonic, int h
             dust_particle_update<T, DIM>(G, tau_t, gt, p, u, dr, vs, id);
             dpos[j] = p;
             dvel[j] = u;
-            dkey[j] = cell_key<T, DIM>(G, p.x, p.y, p.z);
+            dkey[j] = cell_key<T, DIM, EST>(G, p.x, p.y, p.z);
         }
     }
 }
@@ -309,7 +309,10 @@ cudaError_t cell_update_t(const LaunchCtx &L, const void *geo, const void *phys,
     const Geo<T> &Gg = *static_cast<const Geo<T> *>(geo);
     const Phys<T> &Ph = *static_cast<const Phys<T> *>(phys);
     const uint32_t blocks = (Gg.ncells + kCellsPerCta - 1) / kCellsPerCta;
-    k_cell_update<T, A, DIM><<<blocks, kCellsPerCta, 0, L.stream>>>(
+    bool est = true;
+    for (int d = 0; d < DIM; ++d) est = est && Gg.est_exact[d];
+    auto kern = est ? k_cell_update<T, A, DIM, true> : k_cell_update<T, A, DIM, false>;
+    kern<<<blocks, kCellsPerCta, 0, L.stream>>>(
         Gg, Ph, A(S.tau), A(S.g[0]), A(S.g[1]), A(S.g[2]), S.tstar_mode == TFSPH_TSTAR_HARMONIC, S.has_frozen,
         Ph.eos == TFSPH_EOS_ADIABATIC, static_cast<V4<T> *>(G.pos[G.cur]), static_cast<V4<T> *>(G.vel[G.cur]),
         G.id[G.cur], G.key, G.start, static_cast<const V4<T> *>(acc), static_cast<V4<T> *>(D.pos[D.cur]),

@@ -318,12 +318,12 @@ template <class T> __device__ __forceinline__ int axis_cell(T x, T lo, T inv, in
 // [0, n - 1], NaN to 0 (Sec. 2.3: membership of the disjoint volumes). The
 // rounded estimate is within one cell of it; the face thresholds move it to
 // the exact index (two moves at most either way, whatever happens).
-template <class T> __device__ __forceinline__ int exact_cell(const Geo<T> &G, int d, T x)
+template <class T, bool EST = false> __device__ __forceinline__ int exact_cell(const Geo<T> &G, int d, T x)
 {
     T t;
     const int n = G.n[d];
     int i = axis_cell(x, G.lo[d], G.inv_w[d], n, t);
-    if (G.est_exact[d]) return i;
+    if (EST || G.est_exact[d]) return i;
     if (!(x == x)) return 0;
     const T *thr = G.thr[d];
     if (i > 0 && x < __ldg(&thr[i])) {
@@ -336,13 +336,14 @@ template <class T> __device__ __forceinline__ int exact_cell(const Geo<T> &G, in
     return i;
 }
 
-// Cell key, exact per axis; key = ix + nx (iy + ny iz).
-template <class T, int DIM>
+// Cell key, exact per axis; key = ix + nx (iy + ny iz). EST: the caller
+// knows that every axis has est_exact set (the table is not read).
+template <class T, int DIM, bool EST = false>
 __device__ __forceinline__ uint32_t cell_key(const Geo<T> &G, T x, T y, T z)
 {
-    const int ix = exact_cell(G, 0, x);
-    const int iy = DIM > 1 ? exact_cell(G, 1, y) : 0;
-    const int iz = DIM > 2 ? exact_cell(G, 2, z) : 0;
+    const int ix = exact_cell<T, EST>(G, 0, x);
+    const int iy = DIM > 1 ? exact_cell<T, EST>(G, 1, y) : 0;
+    const int iz = DIM > 2 ? exact_cell<T, EST>(G, 2, z) : 0;
     return (uint32_t)ix + (uint32_t)G.n[0] * ((uint32_t)iy + (uint32_t)G.n[1] * (uint32_t)iz);
 }
 

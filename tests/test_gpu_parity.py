@@ -190,18 +190,22 @@ def test_fp32_path_terminal_slip_at_tau_over_tstop_1e6(orc, cell_acc):
     """FP32 path, t_stop = tau / 1e6, on the settling column (gas held by its
     pressure against gravity, dust sinking through it; Sec. 2.3's
     asymptotic-preserving limit): one step against the oracle, and per drag
-    cell the new slip u*' - v*' of the GPU's particle velocities against the
-    implicit cell solve evaluated in binary64 from the step's inputs and the
-    GPU's own pressure force, -(w + tau Abar) / (1 + tau (1 + eps*)/t*), whose
-    limit is t* (-Abar)/(1 + eps*) ~ g t*. FP64 cell sums and factors
-    (cell_acc 1) keep that slip (along g) to 1e-2 normwise over the drag cells,
-    the resolution of the FP32 velocities it is read from; FP32
-    cell sums (cell_acc 0) lose it to the cancellation of tau g against
-    (tau/t*) w' in u*' (measured and printed, gated only loosely)."""
+    cell the new slip u*' - v*' along g, read from the GPU's FP32 particle
+    velocities, against the implicit cell solve evaluated in binary64 from the
+    step's inputs and the GPU's own pressure force,
+    -(w + tau Abar) / (1 + tau (1 + eps*)/t*), and against the oracle's own
+    slip. The slip (~6e-9) is read from velocities up to ~1e-2, so each cell
+    is allowed 1e-2 of its slip plus the FP32 resolution of its two mean
+    velocities. The limit of the solve, t* (-Abar)/(1 + eps*), is g t* up
+    to the column's force balance (the SPH pressure force exceeds gravity by
+    8 % at this resolution). The new slip is solved first and the means
+    follow from it, so FP32 cell sums keep the limit too; the FP64 cell sums
+    change the common mixture velocity, not the slip."""
     w = workloads.column2d(nside=64, precision=0, nsteps=1)
     w.tstop[:] = np.float32(w.tau / 1e6)
     gpu, r, errs = _compare(orc, w, cell_acc=cell_acc)
     p = oracle_params(w)
+    _, s_or, r_or, _ = oracle_step(orc, w)
     ncells = len(r.cstart_g) - 1
     moving = w.frozen == 0
     kg, kd = r.keys_g[moving], r.keys_d
@@ -211,32 +215,26 @@ def test_fp32_path_terminal_slip_at_tau_over_tstop_1e6(orc, cell_acc):
     mean = lambda v, k, cnt: np.bincount(k, weights=v, minlength=ncells) / np.maximum(cnt, 1)
     eps = p.m_dust * L / (p.m_gas * np.maximum(N, 1))
     tst = mean(w.tstop, kd, L)
-    worst = 0.0
-    for ax in range(2):
-        w0 = mean(w.gv[ax, moving], kg, N) - mean(w.du[ax], kd, L)
-        abar = mean(gpu["acc_g"][ax, moving], kg, N)
-        wn = (w0 + w.tau * abar) / (1.0 + w.tau * (1.0 + eps) / np.maximum(tst, 1e-300))
-        slip = mean(gpu["du"][ax], kd, L) - mean(gpu["gv"][ax, moving], kg, N)
-        ref = -wn
-        # normwise over the drag cells, along gravity: across it the slip is ~1e-12, below the
-        # resolution of FP32 velocities of ~1e-6
-        rel = np.linalg.norm((slip - ref)[drag]) / np.linalg.norm(ref[drag])
-        if ax == 1:
-            worst = float(rel)
-        if ax == 1:
-            # the asymptotic limit: the sink speed of the dust relative to the gas is g t*
-            lim = tst * (-abar) / (1.0 + eps)
-            assert np.median(np.abs(ref - lim)[drag] / np.abs(lim[drag])) < 1e-2
-            # the column's SPH pressure force balances gravity to within ~10 % at this resolution
-            ratio = float(np.median(ref[drag] / (w.g[1] * tst[drag])))
-            assert ratio == pytest.approx(1.0, rel=0.15)
-    print(f"terminal slip, cell_acc={cell_acc}: normwise error {worst:.3e}, slip / (g t*) {ratio:.4f}")
-    if cell_acc == 1:
-        # the floor is the FP32 storage of the new velocities (~4.5e-4, ulp 2.9e-11) against a
-        # slip of ~5.6e-9: about 2e-3 normwise over the cells
-        assert worst < 1e-2
-    else:
-        assert worst < 1.0
+    ax = 1
+    w0 = mean(w.gv[ax, moving], kg, N) - mean(w.du[ax], kd, L)
+    abar = mean(gpu["acc_g"][ax, moving], kg, N)
+    ref = -(w0 + w.tau * abar) / (1.0 + w.tau * (1.0 + eps) / np.maximum(tst, 1e-300))
+    vbar = mean(gpu["gv"][ax, moving], kg, N)
+    ubar = mean(gpu["du"][ax], kd, L)
+    slip = ubar - vbar
+    oslip = mean(s_or.du[ax], kd, L) - mean(s_or.gv[ax, moving], kg, N)
+    res = np.spacing(np.abs(vbar).astype(np.float32)).astype(np.float64) + \
+        np.spacing(np.abs(ubar).astype(np.float32)).astype(np.float64)
+    for name, want in (("cell solve", ref), ("oracle", oslip)):
+        excess = (np.abs(slip - want) / (1e-2 * np.abs(want) + 4.0 * res))[drag]
+        print(f"terminal slip, cell_acc={cell_acc}, vs {name}: median relative error "
+              f"{np.median(np.abs(slip - want)[drag] / np.abs(want[drag])):.3e}, max error / bound {excess.max():.3f}")
+        assert excess.max() <= 1.0
+    lim = tst * (-abar) / (1.0 + eps)
+    assert np.median(np.abs(ref - lim)[drag] / np.abs(lim[drag])) < 1e-2
+    ratio = float(np.median(ref[drag] / (w.g[1] * tst[drag])))
+    print(f"terminal slip / (g t*): {ratio:.4f}")
+    assert ratio == pytest.approx(1.0, rel=0.15)
 
 
 # ---------------------------------------------------------------------------
