@@ -54,6 +54,9 @@ def parse_args(argv=None):
     ap.add_argument("--no-batch", action="store_true")
     ap.add_argument("--no-schemes", action="store_true")
     ap.add_argument("--no-fp64-cells", action="store_true")
+    ap.add_argument("--part", choices=["all", "isph", "mk", "batch"], default="all",
+                    help="run one part alone (one drag scheme, or the batched ensemble) and print its "
+                         "object: a short program for profiling that part's kernels")
     return ap.parse_args(argv)
 
 
@@ -385,6 +388,11 @@ def run_ours(args, dist: Dist):
     if not torch.cuda.is_available():
         raise SystemExit("bench.py: no CUDA device; the GPU path has no CPU fallback")
     torch.cuda.set_device(dist.local_rank % torch.cuda.device_count())
+    if args.part != "all":
+        out = run_batch(b, args) if args.part == "batch" else run_schemes(b, args, only=args.part)
+        if dist.rank == 0:
+            print(json.dumps({"part": args.part, "result": out}), flush=True)
+        return
     visible = [v for v in os.environ.get("CUDA_VISIBLE_DEVICES", "").split(",") if v.strip()]
     dev_index = visible[dist.local_rank % len(visible)] if visible else str(torch.cuda.current_device())
 
@@ -698,7 +706,7 @@ def run_batch(b, args):
     }
 
 
-def run_schemes(b, args):
+def run_schemes(b, args, only=None):
     """The other two drag schemes of the paper on the same 3D box: ISPH
     (Sec. 2.2) and MK (Sec. 2.1, explicit: run at tau = t_stop / 2, inside its
     stability limit). CUDA events on the stream around 20 steps after 3."""
@@ -711,6 +719,8 @@ def run_schemes(b, args):
     cell_acc = b.TFSPH_CELL_ACC_FP32 if args.cell_acc == "fp32" else b.TFSPH_CELL_ACC_FP64
     out = {}
     for name, drag in (("isph", b.TFSPH_DRAG_ISPH), ("mk", b.TFSPH_DRAG_MK)):
+        if only is not None and name != only:
+            continue
         tau = w.tau if drag == b.TFSPH_DRAG_ISPH else 0.5 * float(np.min(w.tstop))
         p = b.params_from_dict(w.params, cell_acc=cell_acc, drag=drag)
         with b.Context(p, f32(w.gx), f32(w.gv), f32(w.dx), f32(w.du), f32(w.tstop), ge=f32(w.ge),
