@@ -132,7 +132,7 @@ template <class T, int MODE> struct PairAcc {
             return;
         }
         if (MODE <= 1) {
-            sum += kernel_w4(approx_sqrt(r2) * G.inv_h);
+            sum += kernel_w4(pair_sqrt(r2) * G.inv_h);
             if (MODE == 1) {
                 ++cnt;
                 fp += (uint64_t)((idb & kIdMask) + 1u) * 0x9E3779B97F4A7C15ull;
@@ -140,8 +140,8 @@ template <class T, int MODE> struct PairAcc {
         } else if (MODE == 2) {
             // isothermal pressure term; (1/r) dW/dr without its factor fnorm,
             // which acc_store applies once together with m_g
-            if (r2 == T(0)) return;  // self or coincident particle: zero gradient
-            const T inv_r = approx_rsqrt(r2);
+            if (!(r2 >= pair_r2_min<T>())) return;  // self or coincident particle: zero gradient
+            const T inv_r = pair_rsqrt(r2);
             const T q = r2 * inv_r * G.inv_h;
             const T a = fmax(T(2) - q, T(0));
             const T g = q < T(1) ? T(-3) + T(2.25) * q : (a * a) * (Ph.hm075 * inv_r);
@@ -150,8 +150,8 @@ template <class T, int MODE> struct PairAcc {
             ay -= s * d[1];
             az -= s * d[2];
         } else {
-            if (r2 == T(0)) return;  // self or coincident particle: zero gradient
-            const T inv_r = approx_rsqrt(r2);
+            if (!(r2 >= pair_r2_min<T>())) return;  // self or coincident particle: zero gradient
+            const T inv_r = pair_rsqrt(r2);
             const T F = kernel_f(G, r2 * inv_r * G.inv_h, G.h * inv_r);  // (1/r) dW/dr
             T coef = qa + pb.w;
             if (MODE == 3) {

@@ -127,17 +127,20 @@ __device__ __forceinline__ int halo_seam(const Geo<T> &G, int k, int c0, int hc)
     return G.per[k] && (g < 0 || g >= G.n[k]);
 }
 
-// Appends the neighbours the density walk finds to the particle's list.
-// Entries beyond cap are counted, and written to the tile's spare row cap
-// (never read), which keeps the store unconditional.
+// Appends the neighbours the density walk finds to the particle's list:
+// entry n goes to slot n mod 4 of group n / 4 (16-bit stores; the force pass
+// reads whole groups). Groups beyond cap entries go to the tile's spare
+// group (never read), which keeps the store unconditional.
 struct NbRec {
-    uint16_t *base;   // entry 0 of the particle
-    uint32_t stride;  // owned_cap ((cap + 1) * owned_cap fits 32 bits)
-    int cap;
+    unsigned long long *base;  // group 0 of the particle
+    uint32_t stride;           // owned_cap ((cap + 1) * owned_cap < 2^31: slot offsets fit 32 bits)
+    int gcap;                  // cap / 4: the spare group
     int n;
     __device__ __forceinline__ void push(int j, bool seam)
     {
-        base[(uint32_t)min(n, cap) * stride] = (uint16_t)((uint32_t)j | (seam ? kNbSeam : 0u));
+        const uint32_t g = (uint32_t)min(n >> 2, gcap);
+        reinterpret_cast<uint16_t *>(base)[((g * stride) << 2) + (uint32_t)(n & 3)] =
+            (uint16_t)((uint32_t)j | (seam ? kNbSeam : 0u));
         ++n;
     }
 };
@@ -295,11 +298,12 @@ __device__ __noinline__ void particle_tile(const Geo<T> G, const Phys<T> Ph, con
     acc_store(A, Ph, a, mass, vel, out_rho, pr_out, out_acc, nullptr, nullptr);
 }
 
-// Pair sums over a particle's recorded list (entries `e[k * st]`, k < n), in
-// the recorded order (SEAMLESS: the tile recorded no seam flags).
+// Pair sums over a particle's recorded list (groups `e[g * st]` of four
+// 16-bit entries, n entries), in the recorded order (SEAMLESS: the tile
+// recorded no seam flags).
 template <class T, int DIM, int MODE, bool SEAMLESS>
 __device__ __forceinline__ void read_list(PairAcc<T, MODE> &A, const Geo<T> &G, const Phys<T> &Ph, const V4<T> &pa,
-                                          const V4<T> *spos, const uint16_t *e, size_t st, int n)
+                                          const V4<T> *spos, const unsigned long long *e, size_t st, int n)
 {
     auto pair = [&](uint32_t cur) {
         const V4<T> pb = spos[cur & 0x7FFFu];
@@ -308,25 +312,38 @@ __device__ __forceinline__ void read_list(PairAcc<T, MODE> &A, const Geo<T> &G, 
                                                     : pair_r2<T, DIM, false>(G, pa, pb, d);
         A.template add<true>(G, Ph, pb, nullptr, T(1), 0u, r2, d);
     };
-    // entries in groups of 8 independent loads through the read-only path,
-    // the next group loaded while the current one is used
-    int q = 0;
-    uint32_t ent[8], nxt[8];
-    if (n >= 8) {
-#pragma unroll
-        for (int u = 0; u < 8; ++u) nxt[u] = __ldg(&e[(size_t)u * st]);
+    auto quad = [&](unsigned long long w) {
+        const uint32_t l = (uint32_t)w, h = (uint32_t)(w >> 32);
+        pair(l & 0xFFFFu);
+        pair(l >> 16);
+        pair(h & 0xFFFFu);
+        pair(h >> 16);
+    };
+    // full groups two at a time through the read-only path, the next two
+    // loaded while the current ones are used; then the partial group
+    const int ng = n >> 2;
+    int g = 0;
+    unsigned long long c0, c1, n0 = 0, n1 = 0;
+    if (ng >= 2) {
+        n0 = __ldg(&e[0]);
+        n1 = __ldg(&e[st]);
     }
-    for (; q + 8 <= n; q += 8) {
-#pragma unroll
-        for (int u = 0; u < 8; ++u) ent[u] = nxt[u];
-        if (q + 16 <= n) {
-#pragma unroll
-            for (int u = 0; u < 8; ++u) nxt[u] = __ldg(&e[(size_t)(q + 8 + u) * st]);
+    for (; g + 2 <= ng; g += 2) {
+        c0 = n0;
+        c1 = n1;
+        if (g + 4 <= ng) {
+            n0 = __ldg(&e[(size_t)(g + 2) * st]);
+            n1 = __ldg(&e[(size_t)(g + 3) * st]);
         }
-#pragma unroll
-        for (int u = 0; u < 8; ++u) pair(ent[u]);
+        quad(c0);
+        quad(c1);
     }
-    for (; q < n; ++q) pair(__ldg(&e[(size_t)q * st]));
+    if (g < ng) quad(__ldg(&e[(size_t)g++ * st]));
+    const int m = n & 3;
+    if (m) {
+        const unsigned long long w = __ldg(&e[(size_t)g * st]);
+        for (int u = 0; u < m; ++u) pair((uint32_t)(w >> (16 * u)) & 0xFFFFu);
+    }
 }
 
 template <class T, int DIM, int MODE>
@@ -444,10 +461,10 @@ k_pair_tile(Geo<T> G, Phys<T> Ph, TileCfg C, const V4<T> *__restrict__ pos, cons
             acc_init(A, Ph, pa, vel, rho, a);
             const bool listed = nbl.idx && p < nbl.owned_cap;
             const size_t oc = (size_t)nbl.owned_cap;
-            const size_t lbase = (size_t)blockIdx.x * (size_t)(nbl.cap + 1) * oc + (size_t)p;
+            const size_t lbase = (size_t)blockIdx.x * (size_t)(nbl.cap / 4 + 1) * oc + (size_t)p;
             if (MODE == 0 && listed) {
                 // density pass: record the neighbours in walk order
-                NbRec rec{nbl.idx + lbase, (uint32_t)oc, nbl.cap, 0};
+                NbRec rec{nbl.idx + lbase, (uint32_t)oc, nbl.cap / 4, 0};
                 if (seamless)
                     walk_tile<T, DIM, MODE, true, true>(A, G, Ph, C, c0, pa, lstart, spos, svel, srho, sid, &rec);
                 else
@@ -456,7 +473,7 @@ k_pair_tile(Geo<T> G, Phys<T> Ph, TileCfg C, const V4<T> *__restrict__ pos, cons
             } else if (MODE == 2 && listed && nbl.cnt[(size_t)blockIdx.x * oc + p] != kNbNone) {
                 // force pass: the density pass's list of this binning, same order
                 const int n = nbl.cnt[(size_t)blockIdx.x * oc + p];
-                const uint16_t *e = nbl.idx + lbase;
+                const unsigned long long *e = nbl.idx + lbase;
                 const size_t st = oc;
                 if (seamless)
                     read_list<T, DIM, MODE, true>(A, G, Ph, pa, spos, e, st, n);
@@ -735,7 +752,8 @@ bool nblist_layout_t(const Geo<T> &G, int dim, int64_t n, int *cap, int *owned_c
     for (int k = 0; k < dim; ++k) owned *= (double)C.T[k];
     const double cap_d = 32.0 * std::ceil(want / 32.0);
     const double oc_d = 32.0 * std::ceil((1.25 * owned + 32.0) / 32.0);
-    // a particle's entries lie within cap * owned_cap of its first (32-bit offsets)
+    // cap is a multiple of 32 (so of the 4 entries of a group); a particle's
+    // 16-bit slots lie within cap * owned_cap + 4 of its first (32-bit offsets)
     if ((cap_d + 1.0) * oc_d >= 2147483648.0) return false;
     *cap = (int)cap_d;
     *owned_cap = (int)oc_d;

@@ -454,12 +454,12 @@ int tfsph_init(tfsph_ctx **out, const tfsph_params *p, const void *const *gas, i
         int cap = 0, oc = 0;
         int64_t tiles = 0;
         if (nblist_layout(c->geo, c->precision, c->dim, n_gas, &cap, &oc, &tiles)) {
-            // cap rows per tile plus one spare row for entries beyond cap
-            const size_t bytes = (size_t)tiles * (size_t)(cap + 1) * (size_t)oc * 2;
+            // cap / 4 groups of four entries per tile plus one spare group
+            const size_t bytes = (size_t)tiles * (size_t)(cap / 4 + 1) * (size_t)oc * 8;
             if (bytes <= ((size_t)16 << 30)) {
                 void *tmp0 = nullptr;
                 if ((rc = dalloc(c, &tmp0, bytes))) return bail(rc);
-                c->nbl.idx = static_cast<uint16_t *>(tmp0);
+                c->nbl.idx = static_cast<unsigned long long *>(tmp0);
                 if ((rc = dalloc(c, &tmp0, (size_t)tiles * (size_t)oc * 2))) return bail(rc);
                 c->nbl.cnt = static_cast<uint16_t *>(tmp0);
                 c->nbl.cap = cap;

@@ -116,15 +116,17 @@ struct PhaseBufs {
 // Compact neighbour list of the gas pair sums, written by the tiled density
 // pass and read by the tiled force pass of the same binning (both passes use
 // the same tiles and visit the owned particles of a tile in the same order).
-// For owned particle p < owned_cap of tile t, entry k is
-// idx[(t * (cap + 1) + k) * owned_cap + p]: the tile-local (shared-memory)
-// index of its k-th neighbour in walk order, bit 15 set for a pair across a
-// periodic seam, so a warp's accesses are contiguous; row cap of each tile is
-// a spare that takes (and drops) the entries beyond cap. cnt[t * owned_cap + p] is the
-// number of entries, or kNbNone when the particle has more than cap
+// An entry is the tile-local (shared-memory) index of a neighbour, bit 15
+// set for a pair across a periodic seam. A particle's entries, in walk
+// order, are packed four to a 64-bit group (entry k at bits 16 (k mod 4) of
+// group k / 4); for owned particle p < owned_cap of tile t, group g is
+// idx[(t * (cap / 4 + 1) + g) * owned_cap + p], so a warp's accesses are
+// contiguous; group cap / 4 of each tile is a spare that takes (and drops)
+// the groups beyond cap (a multiple of 4) entries. cnt[t * owned_cap + p] is
+// the number of entries, or kNbNone when the particle has more than cap
 // neighbours; such particles (and p >= owned_cap) walk their candidates again.
 struct NbList {
-    uint16_t *idx = nullptr;
+    unsigned long long *idx = nullptr;
     uint16_t *cnt = nullptr;
     int cap = 0;
     int owned_cap = 0;
@@ -387,6 +389,29 @@ __device__ __forceinline__ float approx_rsqrt(float x)
 __device__ __forceinline__ double approx_rsqrt(double x) { return 1.0 / sqrt(x); }
 __device__ __forceinline__ float approx_div(float a, float b) { return __fdividef(a, b); }
 __device__ __forceinline__ double approx_div(double a, double b) { return a / b; }
+
+// Square root and reciprocal square root of a pair's r^2, with subnormal
+// inputs flushed to zero (no rescaling of subnormal inputs, which the forms
+// above carry): the pair sums treat r^2 below pair_r2_min() (the smallest
+// normal binary32 number; the smallest subnormal in binary64) as a zero
+// displacement.
+__device__ __forceinline__ float pair_sqrt(float x)
+{
+    float r;
+    asm("sqrt.approx.ftz.f32 %0, %1;" : "=f"(r) : "f"(x));
+    return r;
+}
+__device__ __forceinline__ double pair_sqrt(double x) { return sqrt(x); }
+__device__ __forceinline__ float pair_rsqrt(float x)
+{
+    float r;
+    asm("rsqrt.approx.ftz.f32 %0, %1;" : "=f"(r) : "f"(x));
+    return r;
+}
+__device__ __forceinline__ double pair_rsqrt(double x) { return 1.0 / sqrt(x); }
+template <class T> __device__ __forceinline__ T pair_r2_min();
+template <> __device__ __forceinline__ float pair_r2_min<float>() { return 1.17549435e-38f; }
+template <> __device__ __forceinline__ double pair_r2_min<double>() { return 4.9406564584124654e-324; }
 
 // Fused multiply-add with one rounding, for the neighbour decision r^2.
 __device__ __forceinline__ float fma_rn(float a, float b, float c) { return __fmaf_rn(a, b, c); }
