@@ -140,8 +140,9 @@ template <class T, int MODE> struct PairAcc {
         } else if (MODE == 2) {
             // isothermal pressure term; (1/r) dW/dr without its factor fnorm,
             // which acc_store applies once together with m_g
-            if (!(r2 >= pair_r2_min<T>())) return;  // self or coincident particle: zero gradient
-            const T inv_r = pair_rsqrt(r2);
+            // self or coincident particle (r^2 below the smallest normal):
+            // 1/r taken as 0, so q = 0, g is finite and s d = 0 (no branch)
+            const T inv_r = r2 >= pair_r2_min<T>() ? pair_rsqrt(r2) : T(0);
             const T q = r2 * inv_r * G.inv_h;
             const T a = fmax(T(2) - q, T(0));
             const T g = q < T(1) ? T(-3) + T(2.25) * q : (a * a) * (Ph.hm075 * inv_r);
