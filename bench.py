@@ -461,12 +461,12 @@ def run_ours(args, dist: Dist):
         peak = float(pk.get("hbm_gbs", 6800.0))
         unit = "GB/s"
     else:
+        # the clock the pair kernels ran at; without samples, the maximum SM
+        # clock (the peaks file's clock under load is that of a power-capped
+        # GEMM, lower than an FP32 ALU kernel runs at)
         mhz, mhz_src = clk.get("sm_mhz"), "SM clock sampled during the timed steps"
         if not mhz:
-            mhz = float(pk.get("clocks_under_load", {}).get("sm_mhz_median", 0) or 0)
-            mhz_src = "SM clock under load from the measured peaks file"
-        if not mhz:
-            mhz, mhz_src = float(pk.get("sm_max_mhz", 2070.0)), "maximum SM clock"
+            mhz, mhz_src = float(pk.get("sm_max_mhz", 2070.0) or 2070.0), "maximum SM clock (clocks not sampled)"
         achieved = amount / (phase_avg[dominant] * 1e-3) / 1e12
         peak = fp32_alu_peak_tflops(sm_count, mhz)
         unit = "TFLOP/s"
