@@ -358,6 +358,9 @@ k_pair_tile(Geo<T> G, Phys<T> Ph, TileCfg C, const V4<T> *__restrict__ pos, cons
     int *lstart = reinterpret_cast<int *>(smem);      // nhalo + 1
     int *rowpref = lstart + C.nhalo + 1;               // nrows + 1
     int *rowg = rowpref + C.nrows + 1;                 // nrows
+    const int nhr = C.H[1] * C.H[2];                   // halo rows (along x)
+    int *hr_first = rowg + C.nrows;                    // nhr: global start of a halo row
+    int *hr_base = hr_first + nhr;                     // nhr + 1: its staged offset
     V4<T> *spos = reinterpret_cast<V4<T> *>(smem + C.offset);
     V4<T> *svel = spos + C.cap;                        // modes staging a second V4
     T *srho = reinterpret_cast<T *>(svel + (ModeUses<MODE>::vel ? C.cap : 0));  // modes staging a scalar
@@ -387,50 +390,103 @@ k_pair_tile(Geo<T> G, Phys<T> Ph, TileCfg C, const V4<T> *__restrict__ pos, cons
         rowg[r] = g;
         rowpref[r] = c;
     }
-    // halo cell counts; a ragged tile needs only ext + 2R halo cells per axis,
-    // which keeps every raw coordinate within (-n, 2n) so one wrap suffices
-    for (int h = tid; h < C.nhalo; h += blockDim.x) {
-        int hx, hy, hz;
-        halo_coords(h, C, hx, hy, hz);
-        const bool inside = hx < ext[0] + 2 * G.R[0] && hy < ext[1] + 2 * G.R[1] && hz < ext[2] + 2 * G.R[2];
-        const int gx = inside ? halo_cell(G, 0, c0[0], hx) : -1;
-        const int gy = DIM > 1 ? halo_cell(G, 1, c0[1], hy) : 0;
-        const int gz = DIM > 2 ? halo_cell(G, 2, c0[2], hz) : 0;
-        int c = 0;
-        if (gx >= 0 && gy >= 0 && gz >= 0) {
-            const uint32_t key = (uint32_t)gx + (uint32_t)G.n[0] * ((uint32_t)gy + (uint32_t)G.n[1] * (uint32_t)gz);
-            c = (int)(start[key + 1] - start[key]);
-        }
-        lstart[h] = c;
-    }
-    __syncthreads();
-    block_scan_smem(lstart, C.nhalo, wsum);
-    block_scan_smem(rowpref, C.nrows, wsum);
-    const int total = lstart[C.nhalo];
-    const int owned = rowpref[C.nrows];
-    const bool tiled = total <= C.cap;
-
-    if (tiled) {
+    // a tile whose halo lies inside the grid on every axis (no wrap, no
+    // cell outside): each halo row of cells is one contiguous range of the
+    // sorted particles, so the rows are counted and copied whole (not for
+    // the full force, whose walk then spills a register)
+    bool interior = MODE != 3;
+#pragma unroll
+    for (int k = 0; k < 3; ++k)
+        if (c0[k] < G.R[k] || c0[k] + ext[k] + G.R[k] > G.n[k]) interior = false;
+    int total;
+    if (interior) {
+        const int gx0 = c0[0] - G.R[0], gy0 = c0[1] - G.R[1], gz0 = c0[2] - G.R[2];
+        // global start of every halo cell (in lstart for now) and the end of each row
         for (int h = tid; h < C.nhalo; h += blockDim.x) {
-            const int j0 = lstart[h], j1 = lstart[h + 1];
-            if (j1 == j0) continue;
             int hx, hy, hz;
             halo_coords(h, C, hx, hy, hz);
-            const int gx = halo_cell(G, 0, c0[0], hx);
-            const int gy = DIM > 1 ? halo_cell(G, 1, c0[1], hy) : 0;
-            const int gz = DIM > 2 ? halo_cell(G, 2, c0[2], hz) : 0;
-            const uint32_t key = (uint32_t)gx + (uint32_t)G.n[0] * ((uint32_t)gy + (uint32_t)G.n[1] * (uint32_t)gz);
-            const uint32_t g0 = start[key];
-            for (int j = j0; j < j1; ++j) {
-                const uint32_t gi = g0 + (uint32_t)(j - j0);
-                spos[j] = pos[gi];
-                if (ModeUses<MODE>::vel) svel[j] = vel[gi];
-                if (ModeUses<MODE>::rho) srho[j] = rho[gi];
-                if (MODE == 1) sid[j] = id[gi];
+            const uint32_t key = (uint32_t)(gx0 + hx) +
+                                 (uint32_t)G.n[0] * ((uint32_t)(gy0 + hy) + (uint32_t)G.n[1] * (uint32_t)(gz0 + hz));
+            lstart[h] = (int)start[key];
+            if (hx == C.H[0] - 1) hr_base[hy + C.H[1] * hz] = (int)start[key + 1];
+        }
+        __syncthreads();
+        for (int r = tid; r < nhr; r += blockDim.x) {
+            const int f = lstart[r * C.H[0]];
+            hr_first[r] = f;
+            hr_base[r] -= f;  // particles in the row
+        }
+        __syncthreads();
+        block_scan_smem(hr_base, nhr, wsum);
+        block_scan_smem(rowpref, C.nrows, wsum);
+        total = hr_base[nhr];
+        // staged offset of every halo cell: its row's offset plus its place in the row
+        for (int h = tid; h < C.nhalo; h += blockDim.x) {
+            const int r = small_div(h, C.H[0], C.invH[0]);
+            lstart[h] = hr_base[r] + lstart[h] - hr_first[r];
+        }
+        if (tid == 0) lstart[C.nhalo] = total;
+        if (total <= C.cap) {
+            // half a warp per row, consecutive lanes on consecutive particles
+            const int lane = tid & 15;
+            for (int r = tid >> 4; r < nhr; r += (int)blockDim.x >> 4) {
+                const int j0 = hr_base[r], m = hr_base[r + 1] - j0;
+                const uint32_t g0 = (uint32_t)hr_first[r];
+                for (int u = lane; u < m; u += 16) {
+                    const uint32_t gi = g0 + (uint32_t)u;
+                    spos[j0 + u] = pos[gi];
+                    if (ModeUses<MODE>::vel) svel[j0 + u] = vel[gi];
+                    if (ModeUses<MODE>::rho) srho[j0 + u] = rho[gi];
+                    if (MODE == 1) sid[j0 + u] = id[gi];
+                }
             }
         }
         __syncthreads();
+    } else {
+        // halo cell counts; a ragged tile needs only ext + 2R halo cells per axis,
+        // which keeps every raw coordinate within (-n, 2n) so one wrap suffices
+        for (int h = tid; h < C.nhalo; h += blockDim.x) {
+            int hx, hy, hz;
+            halo_coords(h, C, hx, hy, hz);
+            const bool inside = hx < ext[0] + 2 * G.R[0] && hy < ext[1] + 2 * G.R[1] && hz < ext[2] + 2 * G.R[2];
+            const int gx = inside ? halo_cell(G, 0, c0[0], hx) : -1;
+            const int gy = DIM > 1 ? halo_cell(G, 1, c0[1], hy) : 0;
+            const int gz = DIM > 2 ? halo_cell(G, 2, c0[2], hz) : 0;
+            int c = 0;
+            if (gx >= 0 && gy >= 0 && gz >= 0) {
+                const uint32_t key = (uint32_t)gx + (uint32_t)G.n[0] * ((uint32_t)gy + (uint32_t)G.n[1] * (uint32_t)gz);
+                c = (int)(start[key + 1] - start[key]);
+            }
+            lstart[h] = c;
+        }
+        __syncthreads();
+        block_scan_smem(lstart, C.nhalo, wsum);
+        block_scan_smem(rowpref, C.nrows, wsum);
+        total = lstart[C.nhalo];
+        if (total <= C.cap) {
+            for (int h = tid; h < C.nhalo; h += blockDim.x) {
+                const int j0 = lstart[h], j1 = lstart[h + 1];
+                if (j1 == j0) continue;
+                int hx, hy, hz;
+                halo_coords(h, C, hx, hy, hz);
+                const int gx = halo_cell(G, 0, c0[0], hx);
+                const int gy = DIM > 1 ? halo_cell(G, 1, c0[1], hy) : 0;
+                const int gz = DIM > 2 ? halo_cell(G, 2, c0[2], hz) : 0;
+                const uint32_t key = (uint32_t)gx + (uint32_t)G.n[0] * ((uint32_t)gy + (uint32_t)G.n[1] * (uint32_t)gz);
+                const uint32_t g0 = start[key];
+                for (int j = j0; j < j1; ++j) {
+                    const uint32_t gi = g0 + (uint32_t)(j - j0);
+                    spos[j] = pos[gi];
+                    if (ModeUses<MODE>::vel) svel[j] = vel[gi];
+                    if (ModeUses<MODE>::rho) srho[j] = rho[gi];
+                    if (MODE == 1) sid[j] = id[gi];
+                }
+            }
+            __syncthreads();
+        }
     }
+    const int owned = rowpref[C.nrows];
+    const bool tiled = total <= C.cap;
 
     // no halo cell across a periodic seam: the walks take the plain path
     bool seamless = true;
@@ -534,7 +590,9 @@ bool plan_tiles(const Geo<T> &G, int dim, double mean, int bytes_pp, int smem_bu
             nh *= H[k];
         }
         const long nrows = (long)Tt[1] * Tt[2];
-        const long table = 4 * (nh + 1 + 2 * nrows + 1);
+        const long nhr = (long)H[1] * H[2];
+        // lstart, the owned rows' prefix and starts, the halo rows' starts and offsets
+        const long table = 4 * (nh + 1 + 2 * nrows + 1 + 2 * nhr + 1);
         const long offset = (table + 63) / 64 * 64;
         const long cap = (smem_budget - offset) / bytes_pp;
         const double expected = mean * (double)nh;
