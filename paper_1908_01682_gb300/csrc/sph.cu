@@ -25,6 +25,10 @@ namespace tfsph {
 namespace {
 
 constexpr int kTileThreads = 256;
+// Shared memory of a tile that stages positions only (density, isothermal
+// force): 4 CTAs per SM, each with its static arrays and the 1 KB the
+// hardware reserves, within the SM's 228 KB.
+constexpr int kTileSmemPos = 55 * 1024;
 
 // One thread per particle, candidates from global memory.
 template <class T, int DIM, int MODE>
@@ -57,6 +61,9 @@ struct TileCfg {
     float invH[2];  // 1 / H0, 1 / H1
 };
 
+// Bytes of the 16-bit halo-cell offsets (nhalo + 1 of them), padded to 4.
+__host__ __device__ constexpr long lstart_bytes(long nhalo) { return (2 * (nhalo + 1) + 3) / 4 * 4; }
+
 // q = floor(x / d) for 0 <= x < 2^22 and 0 < d < 2^10 by a float multiply with
 // the rounded reciprocal: (x + 1/2)/d lies at least 1/(2d) from an integer,
 // more than the product's rounding error, so the truncation is exact.
@@ -75,8 +82,10 @@ __device__ __forceinline__ void halo_coords(int h, const TileCfg &C, int &hx, in
 }
 
 // In-place exclusive scan of m values in shared memory by the whole block;
-// a[m] receives the total.
-__device__ void block_scan_smem(int *a, int m, int *wsum)
+// a[m] receives the total, which is also returned (exact in int when the
+// 16-bit form truncates the stored sums).
+template <class E>
+__device__ int block_scan_smem(E *a, int m, int *wsum)
 {
     const int tid = threadIdx.x, nth = blockDim.x;
     const int chunk = (m + nth - 1) / nth;
@@ -102,14 +111,16 @@ __device__ void block_scan_smem(int *a, int m, int *wsum)
         if (lane < (nth >> 5)) wsum[lane] = t;
     }
     __syncthreads();
+    const int total = wsum[(nth >> 5) - 1];
     int run = (wid > 0 ? wsum[wid - 1] : 0) + x - s;
     for (int i = b0; i < b1; ++i) {
         const int v = a[i];
-        a[i] = run;
+        a[i] = (E)run;
         run += v;
     }
-    if (tid == nth - 1) a[m] = run;
+    if (tid == nth - 1) a[m] = (E)run;
     __syncthreads();
+    return total;
 }
 
 // Global cell coordinate of halo coordinate hc along axis k (-1: none).
@@ -176,7 +187,7 @@ __device__ __forceinline__ void walk_smem_range(PairAcc<T, MODE> &A, const Geo<T
 // tile lies across a periodic seam, so every row is one plain range).
 template <class T, int DIM, int MODE, bool REC, bool SEAMLESS>
 __device__ __forceinline__ void walk_tile(PairAcc<T, MODE> &A, const Geo<T> &G, const Phys<T> &Ph, const TileCfg &C,
-                                          const int c0[3], const V4<T> &pa, const int *lstart, const V4<T> *spos,
+                                          const int c0[3], const V4<T> &pa, const uint16_t *lstart, const V4<T> *spos,
                                           const V4<T> *svel, const T *srho, const uint32_t *sid, NbRec *rec)
 {
     T tx_, ty_ = T(0), tz_ = T(0);
@@ -286,7 +297,7 @@ __device__ __noinline__ void particle_global(const Geo<T> G, const Phys<T> Ph, u
 // the call's register saves cost more than they free.)
 template <class T, int DIM, int MODE, bool SEAMLESS>
 __device__ __noinline__ void particle_tile(const Geo<T> G, const Phys<T> Ph, const TileCfg C, int c0x, int c0y,
-                                           int c0z, const V4<T> pa, uint32_t a, const int *lstart,
+                                           int c0z, const V4<T> pa, uint32_t a, const uint16_t *lstart,
                                            const V4<T> *spos, const V4<T> *__restrict__ vel, T mass,
                                            T *__restrict__ out_rho, T *pr_out, V4<T> *__restrict__ out_acc)
 {
@@ -355,8 +366,10 @@ k_pair_tile(Geo<T> G, Phys<T> Ph, TileCfg C, const V4<T> *__restrict__ pos, cons
 {
     extern __shared__ __align__(64) unsigned char smem[];
     __shared__ int wsum[kTileThreads / 32];
-    int *lstart = reinterpret_cast<int *>(smem);      // nhalo + 1
-    int *rowpref = lstart + C.nhalo + 1;               // nrows + 1
+    // staged offset of every halo cell (16 bits: a staged tile holds at most
+    // cap <= 0x7FFF particles), then 32-bit tables
+    uint16_t *lstart = reinterpret_cast<uint16_t *>(smem);                     // nhalo + 1
+    int *rowpref = reinterpret_cast<int *>(smem + lstart_bytes(C.nhalo));      // nrows + 1
     int *rowg = rowpref + C.nrows + 1;                 // nrows
     const int nhr = C.H[1] * C.H[2];                   // halo rows (along x)
     int *hr_first = rowg + C.nrows;                    // nhr: global start of a halo row
@@ -394,38 +407,40 @@ k_pair_tile(Geo<T> G, Phys<T> Ph, TileCfg C, const V4<T> *__restrict__ pos, cons
     // cell outside): each halo row of cells is one contiguous range of the
     // sorted particles, so the rows are counted and copied whole (not for
     // the full force, whose walk then spills a register)
-    bool interior = MODE != 3;
+    bool interior = MODE != 3 && C.nhalo * 4 <= C.cap * (int)sizeof(V4<T>);
 #pragma unroll
     for (int k = 0; k < 3; ++k)
         if (c0[k] < G.R[k] || c0[k] + ext[k] + G.R[k] > G.n[k]) interior = false;
     int total;
     if (interior) {
+        // the particle area serves as scratch for the global starts until the copy
+        int *raw = reinterpret_cast<int *>(smem + C.offset);
         const int gx0 = c0[0] - G.R[0], gy0 = c0[1] - G.R[1], gz0 = c0[2] - G.R[2];
-        // global start of every halo cell (in lstart for now) and the end of each row
+        // global start of every halo cell and the end of each row
         for (int h = tid; h < C.nhalo; h += blockDim.x) {
             int hx, hy, hz;
             halo_coords(h, C, hx, hy, hz);
             const uint32_t key = (uint32_t)(gx0 + hx) +
                                  (uint32_t)G.n[0] * ((uint32_t)(gy0 + hy) + (uint32_t)G.n[1] * (uint32_t)(gz0 + hz));
-            lstart[h] = (int)start[key];
+            raw[h] = (int)start[key];
             if (hx == C.H[0] - 1) hr_base[hy + C.H[1] * hz] = (int)start[key + 1];
         }
         __syncthreads();
         for (int r = tid; r < nhr; r += blockDim.x) {
-            const int f = lstart[r * C.H[0]];
+            const int f = raw[r * C.H[0]];
             hr_first[r] = f;
             hr_base[r] -= f;  // particles in the row
         }
         __syncthreads();
-        block_scan_smem(hr_base, nhr, wsum);
+        total = block_scan_smem(hr_base, nhr, wsum);
         block_scan_smem(rowpref, C.nrows, wsum);
-        total = hr_base[nhr];
         // staged offset of every halo cell: its row's offset plus its place in the row
         for (int h = tid; h < C.nhalo; h += blockDim.x) {
             const int r = small_div(h, C.H[0], C.invH[0]);
-            lstart[h] = hr_base[r] + lstart[h] - hr_first[r];
+            lstart[h] = (uint16_t)(hr_base[r] + raw[h] - hr_first[r]);
         }
-        if (tid == 0) lstart[C.nhalo] = total;
+        if (tid == 0) lstart[C.nhalo] = (uint16_t)total;
+        __syncthreads();  // the copy overwrites the scratch
         if (total <= C.cap) {
             // half a warp per row, consecutive lanes on consecutive particles
             const int lane = tid & 15;
@@ -452,17 +467,17 @@ k_pair_tile(Geo<T> G, Phys<T> Ph, TileCfg C, const V4<T> *__restrict__ pos, cons
             const int gx = inside ? halo_cell(G, 0, c0[0], hx) : -1;
             const int gy = DIM > 1 ? halo_cell(G, 1, c0[1], hy) : 0;
             const int gz = DIM > 2 ? halo_cell(G, 2, c0[2], hz) : 0;
-            int c = 0;
+            uint32_t c = 0;
             if (gx >= 0 && gy >= 0 && gz >= 0) {
                 const uint32_t key = (uint32_t)gx + (uint32_t)G.n[0] * ((uint32_t)gy + (uint32_t)G.n[1] * (uint32_t)gz);
-                c = (int)(start[key + 1] - start[key]);
+                c = start[key + 1] - start[key];
             }
-            lstart[h] = c;
+            // a count that does not fit 16 bits makes the tile exceed cap anyway
+            lstart[h] = (uint16_t)min(c, 0xFFFFu);
         }
         __syncthreads();
-        block_scan_smem(lstart, C.nhalo, wsum);
+        total = block_scan_smem(lstart, C.nhalo, wsum);
         block_scan_smem(rowpref, C.nrows, wsum);
-        total = lstart[C.nhalo];
         if (total <= C.cap) {
             for (int h = tid; h < C.nhalo; h += blockDim.x) {
                 const int j0 = lstart[h], j1 = lstart[h + 1];
@@ -565,17 +580,20 @@ template <class T, int MODE> constexpr int tile_bytes_per_particle()
            (ModeUses<MODE>::rho ? (int)sizeof(T) : 0) + (MODE == 1 ? 4 : 0);
 }
 
-// Tile shape for a phase with `mean` particles per cell. Each CTA thread
-// takes one owned particle, so a tile is sized to hold about 7/8 of the
-// block's threads on average (a tile holding more than one particle per
-// thread runs a second, mostly idle pass); its halo must fill at most 80 %
-// of the shared-memory capacity. Returns false when an axis wraps fully.
+// Tile shape for a phase with `mean` particles per cell. The CTA's threads
+// take the owned particles in turn; a tile is sized to hold about 1.55 of
+// them per thread on average, since the halo of R cells around it is staged
+// per tile (in 3D with R = 3: 8 halo cells per owned cell for 6^3 owned
+// cells, 6.0 for 8 x 7 x 7) and a larger tile spreads that over more
+// particles; its
+// halo must fill at most 80 % of the shared-memory capacity. Returns false
+// when an axis wraps fully.
 template <class T>
 bool plan_tiles(const Geo<T> &G, int dim, double mean, int bytes_pp, int smem_budget, TileCfg &C, size_t &smem)
 {
     for (int k = 0; k < dim; ++k)
         if (G.full[k]) return false;
-    const double target_cells = std::max(1.0, 0.875 * kTileThreads / std::max(mean, 1e-6));
+    const double target_cells = std::max(1.0, 1.55 * kTileThreads / std::max(mean, 1e-6));
     const int side = std::max(1, (int)std::floor(std::pow(target_cells, 1.0 / dim) + 1e-9));
     int Tt[3] = {1, 1, 1};
     for (int k = 1; k < dim; ++k) Tt[k] = std::min(side, G.n[k]);
@@ -591,8 +609,9 @@ bool plan_tiles(const Geo<T> &G, int dim, double mean, int bytes_pp, int smem_bu
         }
         const long nrows = (long)Tt[1] * Tt[2];
         const long nhr = (long)H[1] * H[2];
-        // lstart, the owned rows' prefix and starts, the halo rows' starts and offsets
-        const long table = 4 * (nh + 1 + 2 * nrows + 1 + 2 * nhr + 1);
+        // the halo cells' 16-bit offsets, the owned rows' prefix and starts,
+        // the halo rows' starts and offsets
+        const long table = lstart_bytes(nh) + 4 * (2 * nrows + 1 + 2 * nhr + 1);
         const long offset = (table + 63) / 64 * 64;
         const long cap = (smem_budget - offset) / bytes_pp;
         const double expected = mean * (double)nh;
@@ -626,7 +645,7 @@ cudaError_t pair_launch(const LaunchCtx &L, const Geo<T> &G, const Phys<T> &Ph, 
                         NbList nb = NbList{})
 {
     constexpr int bpp = tile_bytes_per_particle<T, MODE>();
-    const int budget = (ModeUses<MODE>::vel || ModeUses<MODE>::rho) ? 72 * 1024 : 52 * 1024;
+    const int budget = (ModeUses<MODE>::vel || ModeUses<MODE>::rho) ? 72 * 1024 : kTileSmemPos;
     TileCfg C{};
     size_t smem = 0;
     if (plan_tiles(G, DIM, mean, bpp, budget, C, smem)) {
@@ -805,7 +824,7 @@ bool nblist_layout_t(const Geo<T> &G, int dim, int64_t n, int *cap, int *owned_c
     // the density pass's tiles (MODE 0 plan)
     TileCfg C{};
     size_t smem = 0;
-    if (!plan_tiles(G, dim, mean, tile_bytes_per_particle<T, 0>(), 52 * 1024, C, smem) || C.cap > 0x7FFF) return false;
+    if (!plan_tiles(G, dim, mean, tile_bytes_per_particle<T, 0>(), kTileSmemPos, C, smem) || C.cap > 0x7FFF) return false;
     double owned = mean;
     for (int k = 0; k < dim; ++k) owned *= (double)C.T[k];
     const double cap_d = 32.0 * std::ceil(want / 32.0);
