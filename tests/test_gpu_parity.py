@@ -14,7 +14,8 @@ Within tolerance after one step, tol = 1e-5 (FP32 path) or 1e-12 (FP64 path):
       |v' - v'_ref| <= tol (|v'_ref| + |v|) + K u tau (S_a + S_cell)
   where S_a is the magnitude sum of particle a's pair terms (reported by the
   oracle), S_cell its mean over the cell's gas, u the unit roundoff of the
-  path (2^-24 or 2^-53) and K = 128. The pressure force of a nearly uniform
+  path (2^-24 or 2^-53) and K = 48 (parity.KAPPA_STEP; the conditioning test
+  below keeps K = 128). The pressure force of a nearly uniform
   state is a small residual of large pair terms; rounding each term in the
   path's precision bounds its accuracy by u S_a, whatever the order of the sum.
 """
