@@ -4,7 +4,7 @@ of the C oracle over a checkpointed multi-step rollout.
 
 Tolerances: FP64 path 1e-9 relative per component (both sides exact up to
 rounding); FP32 path 1e-3 relative normwise; finite differences 1e-4
-relative (the spec agreement).
+relative (the agreement asked of the differentiable rollout).
 """
 import numpy as np
 import pytest
@@ -202,7 +202,7 @@ def test_dust_profile_matches_oracle(orc, prec):
 
 
 def test_profile_loss_rollout_matches_finite_differences(orc):
-    """The spec gradient on a small settling column (FP64): the squared
+    """The rollout's gradient on a small settling column (FP64): the squared
     error of the final binned dust density (8 x 8 bins) against a seeded
     target after 20 steps checkpointed every 7, with respect to per-particle
     t_stop and the initial gas and dust velocities, against central
