@@ -57,16 +57,17 @@ __device__ __forceinline__ int cell_drag_solve(const Phys<T> &Ph, A tau, const A
     for (uint32_t j = ds + 1; j < de; ++j) add_dust(dvel[j]);
     if (!(N > A(0) && L > A(0))) return 0;
     const A eps = A(Ph.m_d) * L / (A(Ph.m_g) * N);
-    const A tst = harmonic ? L / st : st / L;
-    const A rt = tau / tst;
-    const A den = A(1) + rt * (A(1) + eps);
     const A invN = A(1) / N, invL = A(1) / L;
+    // rt = tau / t*, with t* = st / L (mean) or L / st (harmonic mean)
+    const A rt = harmonic ? tau * st * invL : tau * L / st;
+    const A den = A(1) + rt * (A(1) + eps);
+    const A invden = A(1) / den;  // one division for the DIM components
 #pragma unroll
     for (int k = 0; k < DIM; ++k) {
         const A vs = sv[k] * invN;
         const A us = su[k] * invL;
         const A ab = sa[k] * invN;
-        const A wn = ((vs - us) + tau * ab) / den;
+        const A wn = ((vs - us) + tau * ab) * invden;
         const A un = us + tau * gv[k] + rt * wn;
         un_out[k] = T(un);
         vn_out[k] = T(un + wn);
