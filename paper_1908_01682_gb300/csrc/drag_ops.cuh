@@ -57,7 +57,9 @@ __device__ __forceinline__ int cell_drag_solve(const Phys<T> &Ph, A tau, const A
     for (uint32_t j = ds + 1; j < de; ++j) add_dust(dvel[j]);
     if (!(N > A(0) && L > A(0))) return 0;
     const A eps = A(Ph.m_d) * L / (A(Ph.m_g) * N);
-    const A invN = A(1) / N, invL = A(1) / L;
+    // 1/N and 1/L from one division (N L is an exact product of counts)
+    const A invNL = A(1) / (N * L);
+    const A invN = L * invNL, invL = N * invNL;
     // rt = tau / t*, with t* = st / L (mean) or L / st (harmonic mean)
     const A rt = harmonic ? tau * st * invL : tau * L / st;
     const A den = A(1) + rt * (A(1) + eps);
@@ -72,8 +74,11 @@ __device__ __forceinline__ int cell_drag_solve(const Phys<T> &Ph, A tau, const A
         un_out[k] = T(un);
         vn_out[k] = T(un + wn);
     }
-    ig_out = T(A(1) / (A(1) + rt * eps));
-    id_out = T(A(1) / (A(1) + rt));
+    // 1/(1 + rt eps) and 1/(1 + rt) from one division
+    const A dg = A(1) + rt * eps, dd = A(1) + rt;
+    const A invgd = A(1) / (dg * dd);
+    ig_out = T(dd * invgd);
+    id_out = T(dg * invgd);
     return 1;
 }
 
