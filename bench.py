@@ -10,7 +10,12 @@ particles leave their initial lattice as the run goes on and the pair sums
 slow down with the disorder, so a shorter window would flatter the step.
 
   python bench.py [--gpus N] [--steps K] [--warmup W] [--workload box3d|dustyshock|column2d]
-                  [--impl ours|reference]
+                  [--impl ours|reference] [--cell-acc fp32|fp64] [--part all|isph|mk|batch]
+                  [--no-cpu-baseline] [--no-e2e] [--no-clocks] [--no-adjoint] [--no-batch]
+                  [--no-schemes] [--no-fp64-cells]
+
+``--part`` runs one part alone (one drag scheme, or the batched ensemble) and
+prints its object: a short program for profiling that part's kernels.
 
 Prints one JSON line (rank 0). Timed region: barrier + synchronize on both
 sides, CUDA events on the library's stream, max over ranks. The state of the
