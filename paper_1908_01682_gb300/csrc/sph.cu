@@ -27,8 +27,8 @@ namespace {
 constexpr int kTileThreads = 256;
 // Shared memory of a tile that stages positions only (density, isothermal
 // force): 4 CTAs per SM, each with its static arrays and the 1 KB the
-// hardware reserves, within the SM's 228 KB.
-constexpr int kTileSmemPos = 55 * 1024;
+// hardware reserves, within the SM's 228 KB (4 x (56832 + 64 + 1024) bytes).
+constexpr int kTileSmemPos = 56832;
 
 // One thread per particle, candidates from global memory.
 template <class T, int DIM, int MODE>
@@ -581,25 +581,38 @@ template <class T, int MODE> constexpr int tile_bytes_per_particle()
 }
 
 // Tile shape for a phase with `mean` particles per cell. The CTA's threads
-// take the owned particles in turn; a tile is sized to hold about 1.55 of
-// them per thread on average, since the halo of R cells around it is staged
-// per tile (in 3D with R = 3: 8 halo cells per owned cell for 6^3 owned
-// cells, 6.0 for 8 x 7 x 7) and a larger tile spreads that over more
-// particles; its
-// halo must fill at most 80 % of the shared-memory capacity. Returns false
-// when an axis wraps fully.
+// take the owned particles in turn; a tile holds about 7/8 of them per
+// thread, or 1.97 (two nearly full passes) where the halo of R cells staged
+// around it outweighs it (in 3D with R = 3: 8 halo cells per owned cell for
+// 6^3 owned cells, 5.5 for 10 x 7 x 7), so that the halo is spread over more
+// particles; in 1D and 2D, with cells of 2h (R = 1), the halo is small and
+// the second pass would cost more than it saves. Its expected halo must fill at most 90 %
+// of the shared-memory capacity (a tile whose halo exceeds it takes the
+// global-memory walk; the 3D box's halos stay within 4 % of their mean).
+// Returns false when an axis wraps fully.
 template <class T>
 bool plan_tiles(const Geo<T> &G, int dim, double mean, int bytes_pp, int smem_budget, TileCfg &C, size_t &smem)
 {
     for (int k = 0; k < dim; ++k)
         if (G.full[k]) return false;
-    const double target_cells = std::max(1.0, 1.55 * kTileThreads / std::max(mean, 1e-6));
-    const int side = std::max(1, (int)std::floor(std::pow(target_cells, 1.0 / dim) + 1e-9));
     int Tt[3] = {1, 1, 1};
-    for (int k = 1; k < dim; ++k) Tt[k] = std::min(side, G.n[k]);
-    double rest = 1.0;
-    for (int k = 1; k < dim; ++k) rest *= Tt[k];
-    Tt[0] = std::max(1, std::min(G.n[0], (int)std::floor(target_cells / rest + 1e-9)));
+    // owned cells for about `per_thread` owned particles per thread
+    auto shape = [&](double per_thread) {
+        const double target_cells = std::max(1.0, per_thread * kTileThreads / std::max(mean, 1e-6));
+        const int side = std::max(1, (int)std::floor(std::pow(target_cells, 1.0 / dim) + 1e-9));
+        Tt[0] = Tt[1] = Tt[2] = 1;
+        for (int k = 1; k < dim; ++k) Tt[k] = std::min(side, G.n[k]);
+        double rest = 1.0;
+        for (int k = 1; k < dim; ++k) rest *= Tt[k];
+        Tt[0] = std::max(1, std::min(G.n[0], (int)std::floor(target_cells / rest + 1e-9)));
+    };
+    // one pass over the owned particles (7/8 of the threads) unless the halo
+    // outweighs the tile (more than 3 halo cells per owned cell, as in 3D
+    // with R = 3), then two nearly full passes to spread it
+    shape(0.875);
+    double halo_ratio = 1.0;
+    for (int k = 0; k < dim; ++k) halo_ratio *= (double)(Tt[k] + 2 * G.R[k]) / (double)Tt[k];
+    if (halo_ratio > 3.0) shape(1.97);
     for (;;) {
         int H[3] = {1, 1, 1};
         long nh = 1;
@@ -618,7 +631,7 @@ bool plan_tiles(const Geo<T> &G, int dim, double mean, int bytes_pp, int smem_bu
         int kmax = 0;
         for (int k = 1; k < dim; ++k)
             if (Tt[k] > Tt[kmax]) kmax = k;
-        if ((cap > 0 && expected <= 0.8 * (double)cap) || Tt[kmax] == 1) {
+        if ((cap > 0 && expected <= 0.9 * (double)cap) || Tt[kmax] == 1) {
             if (cap <= 0 || nh >= (1L << 22) || H[0] >= 1024 || H[1] >= 1024) return false;
             for (int k = 0; k < 3; ++k) {
                 C.T[k] = Tt[k];
