@@ -187,13 +187,16 @@ __device__ __forceinline__ void walk_smem_range(PairAcc<T, MODE> &A, const Geo<T
 // tile lies across a periodic seam, so every row is one plain range).
 template <class T, int DIM, int MODE, bool REC, bool SEAMLESS>
 __device__ __forceinline__ void walk_tile(PairAcc<T, MODE> &A, const Geo<T> &G, const Phys<T> &Ph, const TileCfg &C,
-                                          const int c0[3], const V4<T> &pa, const uint16_t *lstart, const V4<T> *spos,
-                                          const V4<T> *svel, const T *srho, const uint32_t *sid, NbRec *rec)
+                                          const int c0[3], const V4<T> &pa, const V4<T> &pc, bool xsplit,
+                                          const uint16_t *lstart, const V4<T> *spos, const V4<T> *svel, const T *srho,
+                                          const uint32_t *sid, NbRec *rec)
 {
+    // pa: the staged (possibly shifted) position the displacements use;
+    // pc: the same position in box coordinates, for its cell and window
     T tx_, ty_ = T(0), tz_ = T(0);
-    const int cx = axis_cell(pa.x, G.lo[0], G.inv_w[0], G.n[0], tx_);
-    const int cy = DIM > 1 ? axis_cell(pa.y, G.lo[1], G.inv_w[1], G.n[1], ty_) : 0;
-    const int cz = DIM > 2 ? axis_cell(pa.z, G.lo[2], G.inv_w[2], G.n[2], tz_) : 0;
+    const int cx = axis_cell(pc.x, G.lo[0], G.inv_w[0], G.n[0], tx_);
+    const int cy = DIM > 1 ? axis_cell(pc.y, G.lo[1], G.inv_w[1], G.n[1], ty_) : 0;
+    const int cz = DIM > 2 ? axis_cell(pc.z, G.lo[2], G.inv_w[2], G.n[2], tz_) : 0;
     const T fx = tx_ - T(cx);
     const T fy = DIM > 1 ? ty_ - T(cy) : T(0);
     const T fz = DIM > 2 ? tz_ - T(cz) : T(0);
@@ -244,6 +247,22 @@ __device__ __forceinline__ void walk_tile(PairAcc<T, MODE> &A, const Geo<T> &G, 
             const int hrow = C.H[0] * ((hy + oy) + C.H[1] * (hz + oz));
             const int u0 = hx + olo, u1 = hx + ohi + 1;  // halo x cells [u0, u1)
             if (SEAMLESS) {
+                // a tile staged with its seam shifts (xsplit: across the x seam)
+                // keeps the seam walk's order: a row that crosses no y or z
+                // seam is walked inside first, then across the low and the
+                // high x seam, so the sums do not depend on the tiling
+                if (xsplit && !((DIM > 1 && halo_seam(G, 1, c0[1], hy + oy)) ||
+                                (DIM > 2 && halo_seam(G, 2, c0[2], hz + oz)))) {
+                    const int a0 = min(max(u0, sx0), u1);
+                    const int a1 = max(min(u1, sx1), a0);
+                    walk_smem_range<T, DIM, MODE, false, REC>(A, G, Ph, pa, spos, svel, srho, sid, lstart[hrow + a0],
+                                                              lstart[hrow + a1], rec);
+                    walk_smem_range<T, DIM, MODE, false, REC>(A, G, Ph, pa, spos, svel, srho, sid, lstart[hrow + u0],
+                                                              lstart[hrow + a0], rec);
+                    walk_smem_range<T, DIM, MODE, false, REC>(A, G, Ph, pa, spos, svel, srho, sid, lstart[hrow + a1],
+                                                              lstart[hrow + u1], rec);
+                    continue;
+                }
                 walk_smem_range<T, DIM, MODE, false, REC>(A, G, Ph, pa, spos, svel, srho, sid, lstart[hrow + u0],
                                                           lstart[hrow + u1], rec);
                 continue;
@@ -297,7 +316,8 @@ __device__ __noinline__ void particle_global(const Geo<T> G, const Phys<T> Ph, u
 // the call's register saves cost more than they free.)
 template <class T, int DIM, int MODE, bool SEAMLESS>
 __device__ __noinline__ void particle_tile(const Geo<T> G, const Phys<T> Ph, const TileCfg C, int c0x, int c0y,
-                                           int c0z, const V4<T> pa, uint32_t a, const uint16_t *lstart,
+                                           int c0z, const V4<T> pa, const V4<T> pc, bool xsplit, uint32_t a,
+                                           const uint16_t *lstart,
                                            const V4<T> *spos, const V4<T> *__restrict__ vel, T mass,
                                            T *__restrict__ out_rho, T *pr_out, V4<T> *__restrict__ out_acc)
 {
@@ -305,7 +325,8 @@ __device__ __noinline__ void particle_tile(const Geo<T> G, const Phys<T> Ph, con
     PairAcc<T, MODE> A;
     acc_init(A, Ph, pa, vel, static_cast<const T *>(nullptr), a);
     const int c0[3] = {c0x, c0y, c0z};
-    walk_tile<T, DIM, MODE, false, SEAMLESS>(A, G, Ph, C, c0, pa, lstart, spos, nullptr, nullptr, nullptr, nullptr);
+    walk_tile<T, DIM, MODE, false, SEAMLESS>(A, G, Ph, C, c0, pa, pc, xsplit, lstart, spos, nullptr, nullptr, nullptr,
+                                             nullptr);
     acc_store(A, Ph, a, mass, vel, out_rho, pr_out, out_acc, nullptr, nullptr);
 }
 
@@ -389,6 +410,43 @@ k_pair_tile(Geo<T> G, Phys<T> Ph, TileCfg C, const V4<T> *__restrict__ pos, cons
     int ext[3];
 #pragma unroll
     for (int k = 0; k < 3; ++k) ext[k] = min(C.T[k], G.n[k] - c0[k]);
+
+    // Periodic seams. A tile whose halo crosses the low seam of axis k stages
+    // its wrapped cells at x - L; one whose halo crosses the high seam stages
+    // its own cells at x - L and its wrapped ones at x. With lo = 0 every such
+    // subtraction is exact (Sterbenz: the coordinates lie within a factor of
+    // two of L, for a high seam because the halo lies in the upper half of
+    // the box), so each pair's displacement is the plain difference of staged
+    // coordinates, the correctly rounded periodic displacement, and the walks
+    // take the plain path. Tiles that do not meet this (lo != 0, a halo over
+    // both seams) keep the per-pair seam path.
+    bool seamless = true, shifted = false, xsplit = false;
+    int lowk[3] = {0, 0, 0}, highk[3] = {0, 0, 0};
+    T orig[3] = {T(0), T(0), T(0)};  // what the owned particles' staged coordinates lack
+    {
+        bool crosses = false, ok = true;
+#pragma unroll
+        for (int k = 0; k < DIM; ++k) {
+            if (!G.per[k]) continue;
+            lowk[k] = c0[k] < G.R[k];
+            highk[k] = c0[k] + ext[k] + G.R[k] > G.n[k];
+            if (lowk[k] || highk[k]) {
+                crosses = true;
+                if (!(G.lo[k] == T(0)) || (lowk[k] && highk[k]) || (highk[k] && 2 * (c0[k] - G.R[k]) < G.n[k]))
+                    ok = false;
+            }
+        }
+        if (crosses) {
+            if (ok) {
+                shifted = true;
+#pragma unroll
+                for (int k = 0; k < DIM; ++k) orig[k] = highk[k] ? G.L[k] : T(0);
+                xsplit = lowk[0] || highk[0];
+            } else {
+                seamless = false;
+            }
+        }
+    }
 
     // owned rows: global start and particle count
     for (int r = tid; r < C.nrows; r += blockDim.x) {
@@ -489,9 +547,23 @@ k_pair_tile(Geo<T> G, Phys<T> Ph, TileCfg C, const V4<T> *__restrict__ pos, cons
                 const int gz = DIM > 2 ? halo_cell(G, 2, c0[2], hz) : 0;
                 const uint32_t key = (uint32_t)gx + (uint32_t)G.n[0] * ((uint32_t)gy + (uint32_t)G.n[1] * (uint32_t)gz);
                 const uint32_t g0 = start[key];
+                // the seam shift of this halo cell (see above)
+                T sh[3] = {T(0), T(0), T(0)};
+                if (shifted) {
+                    const int hk[3] = {hx, hy, hz};
+#pragma unroll
+                    for (int k = 0; k < DIM; ++k) {
+                        const int raw = c0[k] - G.R[k] + hk[k];
+                        if ((highk[k] && raw < G.n[k]) || (lowk[k] && raw < 0)) sh[k] = G.L[k];
+                    }
+                }
                 for (int j = j0; j < j1; ++j) {
                     const uint32_t gi = g0 + (uint32_t)(j - j0);
-                    spos[j] = pos[gi];
+                    V4<T> q = pos[gi];
+                    q.x = sub_rn(q.x, sh[0]);
+                    if (DIM > 1) q.y = sub_rn(q.y, sh[1]);
+                    if (DIM > 2) q.z = sub_rn(q.z, sh[2]);
+                    spos[j] = q;
                     if (ModeUses<MODE>::vel) svel[j] = vel[gi];
                     if (ModeUses<MODE>::rho) srho[j] = rho[gi];
                     if (MODE == 1) sid[j] = id[gi];
@@ -503,11 +575,6 @@ k_pair_tile(Geo<T> G, Phys<T> Ph, TileCfg C, const V4<T> *__restrict__ pos, cons
     const int owned = rowpref[C.nrows];
     const bool tiled = total <= C.cap;
 
-    // no halo cell across a periodic seam: the walks take the plain path
-    bool seamless = true;
-#pragma unroll
-    for (int k = 0; k < DIM; ++k)
-        if (G.per[k] && (c0[k] < G.R[k] || c0[k] + ext[k] + G.R[k] > G.n[k])) seamless = false;
 
     for (int p = tid; p < owned; p += blockDim.x) {
         // owned row of p: the last r with rowpref[r] <= p
@@ -529,6 +596,12 @@ k_pair_tile(Geo<T> G, Phys<T> Ph, TileCfg C, const V4<T> *__restrict__ pos, cons
             const int oy = lo % C.T[1], oz = lo / C.T[1];
             const int hrow = C.H[0] * ((oy + (DIM > 1 ? G.R[1] : 0)) + C.H[1] * (oz + (DIM > 2 ? G.R[2] : 0)));
             const V4<T> pa = spos[lstart[hrow + G.R[0]] + k];
+            V4<T> pc = pa;  // box coordinates (adding back the shift is exact)
+            if (shifted) {
+                pc.x = add_rn(pa.x, orig[0]);
+                if (DIM > 1) pc.y = add_rn(pa.y, orig[1]);
+                if (DIM > 2) pc.z = add_rn(pa.z, orig[2]);
+            }
             acc_init(A, Ph, pa, vel, rho, a);
             const bool listed = nbl.idx && p < nbl.owned_cap;
             const size_t oc = (size_t)nbl.owned_cap;
@@ -537,9 +610,9 @@ k_pair_tile(Geo<T> G, Phys<T> Ph, TileCfg C, const V4<T> *__restrict__ pos, cons
                 // density pass: record the neighbours in walk order
                 NbRec rec{nbl.idx + lbase, (uint32_t)oc, nbl.cap / 4, 0};
                 if (seamless)
-                    walk_tile<T, DIM, MODE, true, true>(A, G, Ph, C, c0, pa, lstart, spos, svel, srho, sid, &rec);
+                    walk_tile<T, DIM, MODE, true, true>(A, G, Ph, C, c0, pa, pc, xsplit, lstart, spos, svel, srho, sid, &rec);
                 else
-                    walk_tile<T, DIM, MODE, true, false>(A, G, Ph, C, c0, pa, lstart, spos, svel, srho, sid, &rec);
+                    walk_tile<T, DIM, MODE, true, false>(A, G, Ph, C, c0, pa, pc, xsplit, lstart, spos, svel, srho, sid, &rec);
                 nbl.cnt[(size_t)blockIdx.x * oc + p] = rec.n <= nbl.cap ? (uint16_t)rec.n : kNbNone;
             } else if (MODE == 2 && listed && nbl.cnt[(size_t)blockIdx.x * oc + p] != kNbNone) {
                 // force pass: the density pass's list of this binning, same order
@@ -554,17 +627,17 @@ k_pair_tile(Geo<T> G, Phys<T> Ph, TileCfg C, const V4<T> *__restrict__ pos, cons
                 // a particle the density pass does not list (rare): out of line
                 if constexpr (MODE == 0) {
                     if (seamless)
-                        particle_tile<T, DIM, MODE, true>(G, Ph, C, c0[0], c0[1], c0[2], pa, a, lstart, spos, vel,
+                        particle_tile<T, DIM, MODE, true>(G, Ph, C, c0[0], c0[1], c0[2], pa, pc, xsplit, a, lstart, spos, vel,
                                                           mass, out_rho, pr_out, out_acc);
                     else
-                        particle_tile<T, DIM, MODE, false>(G, Ph, C, c0[0], c0[1], c0[2], pa, a, lstart, spos, vel,
+                        particle_tile<T, DIM, MODE, false>(G, Ph, C, c0[0], c0[1], c0[2], pa, pc, xsplit, a, lstart, spos, vel,
                                                            mass, out_rho, pr_out, out_acc);
                 }
                 continue;
             } else if (seamless) {
-                walk_tile<T, DIM, MODE, false, true>(A, G, Ph, C, c0, pa, lstart, spos, svel, srho, sid, nullptr);
+                walk_tile<T, DIM, MODE, false, true>(A, G, Ph, C, c0, pa, pc, xsplit, lstart, spos, svel, srho, sid, nullptr);
             } else {
-                walk_tile<T, DIM, MODE, false, false>(A, G, Ph, C, c0, pa, lstart, spos, svel, srho, sid, nullptr);
+                walk_tile<T, DIM, MODE, false, false>(A, G, Ph, C, c0, pa, pc, xsplit, lstart, spos, svel, srho, sid, nullptr);
             }
         }
         acc_store(A, Ph, a, mass, vel, out_rho, pr_out, out_acc, cnt, fpr);
