@@ -184,12 +184,14 @@ __device__ __forceinline__ void walk_smem_range(PairAcc<T, MODE> &A, const Geo<T
 
 // Candidate walk of one owned particle over the staged tile (REC: the
 // density pass recording the neighbour list; SEAMLESS: no halo cell of the
-// tile lies across a periodic seam, so every row is one plain range).
+// tile lies across a periodic seam, or the tile was staged with its seam
+// shifts, so every row is one plain range). Each row is walked in the order
+// of its staged cells in either case.
 template <class T, int DIM, int MODE, bool REC, bool SEAMLESS>
 __device__ __forceinline__ void walk_tile(PairAcc<T, MODE> &A, const Geo<T> &G, const Phys<T> &Ph, const TileCfg &C,
-                                          const int c0[3], const V4<T> &pa, const V4<T> &pc, bool xsplit,
-                                          const uint16_t *lstart, const V4<T> *spos, const V4<T> *svel, const T *srho,
-                                          const uint32_t *sid, NbRec *rec)
+                                          const int c0[3], const V4<T> &pa, const V4<T> &pc, const uint16_t *lstart,
+                                          const V4<T> *spos, const V4<T> *svel, const T *srho, const uint32_t *sid,
+                                          NbRec *rec)
 {
     // pa: the staged (possibly shifted) position the displacements use;
     // pc: the same position in box coordinates, for its cell and window
@@ -247,46 +249,30 @@ __device__ __forceinline__ void walk_tile(PairAcc<T, MODE> &A, const Geo<T> &G, 
             const int hrow = C.H[0] * ((hy + oy) + C.H[1] * (hz + oz));
             const int u0 = hx + olo, u1 = hx + ohi + 1;  // halo x cells [u0, u1)
             if (SEAMLESS) {
-                // a tile staged with its seam shifts (xsplit: across the x seam)
-                // keeps the seam walk's order: a row that crosses no y or z
-                // seam is walked inside first, then across the low and the
-                // high x seam, so the sums do not depend on the tiling
-                if (xsplit && !((DIM > 1 && halo_seam(G, 1, c0[1], hy + oy)) ||
-                                (DIM > 2 && halo_seam(G, 2, c0[2], hz + oz)))) {
-                    const int a0 = min(max(u0, sx0), u1);
-                    const int a1 = max(min(u1, sx1), a0);
-                    walk_smem_range<T, DIM, MODE, false, REC>(A, G, Ph, pa, spos, svel, srho, sid, lstart[hrow + a0],
-                                                              lstart[hrow + a1], rec);
-                    walk_smem_range<T, DIM, MODE, false, REC>(A, G, Ph, pa, spos, svel, srho, sid, lstart[hrow + u0],
-                                                              lstart[hrow + a0], rec);
-                    walk_smem_range<T, DIM, MODE, false, REC>(A, G, Ph, pa, spos, svel, srho, sid, lstart[hrow + a1],
-                                                              lstart[hrow + u1], rec);
-                    continue;
-                }
                 walk_smem_range<T, DIM, MODE, false, REC>(A, G, Ph, pa, spos, svel, srho, sid, lstart[hrow + u0],
                                                           lstart[hrow + u1], rec);
                 continue;
             }
-            // [u0, a0) across the low seam, [a0, a1) inside, [a1, u1) across the high seam
+            // [u0, a0) across the low seam, [a0, a1) inside, [a1, u1) across the
+            // high seam, in that order (the order of the staged cells, as in the
+            // tiles staged with their seam shifts); a row across a y or z seam
+            // takes the two-sum displacement over its whole range
             const int a0 = min(max(u0, sx0), u1);
             const int a1 = max(min(u1, sx1), a0);
-            const bool inner_seam = (seam_y | seam_z) != 0;
-            if (!inner_seam && a1 > a0)
+            if (seam_y | seam_z) {
+                walk_smem_range<T, DIM, MODE, true, REC>(A, G, Ph, pa, spos, svel, srho, sid, lstart[hrow + u0],
+                                                         lstart[hrow + u1], rec);
+                continue;
+            }
+            if (a0 > u0)
+                walk_smem_range<T, DIM, MODE, true, REC>(A, G, Ph, pa, spos, svel, srho, sid, lstart[hrow + u0],
+                                                         lstart[hrow + a0], rec);
+            if (a1 > a0)
                 walk_smem_range<T, DIM, MODE, false, REC>(A, G, Ph, pa, spos, svel, srho, sid, lstart[hrow + a0],
                                                           lstart[hrow + a1], rec);
-            if (inner_seam || a0 > u0 || u1 > a1) {
-                // the rare ranges across a seam, visited with the two-sum displacement
-                const int j0 = lstart[hrow + (inner_seam ? u0 : (a0 > u0 ? u0 : a1))];
-                const int j1 = lstart[hrow + (inner_seam ? u1 : (u1 > a1 ? u1 : a0))];
-                const int jm0 = (!inner_seam && a0 > u0 && u1 > a1) ? lstart[hrow + a0] : j1;
-                const int jm1 = (!inner_seam && a0 > u0 && u1 > a1) ? lstart[hrow + a1] : j1;
-                // [j0, jm0) and [jm1, j1): the inner part [jm0, jm1) was visited above
-                for (int j = j0; j < j1; ++j) {
-                    if (j == jm0) j = jm1;
-                    if (j >= j1) break;
-                    walk_smem_range<T, DIM, MODE, true, REC>(A, G, Ph, pa, spos, svel, srho, sid, j, j + 1, rec);
-                }
-            }
+            if (u1 > a1)
+                walk_smem_range<T, DIM, MODE, true, REC>(A, G, Ph, pa, spos, svel, srho, sid, lstart[hrow + a1],
+                                                         lstart[hrow + u1], rec);
         }
     }
 }
@@ -316,8 +302,7 @@ __device__ __noinline__ void particle_global(const Geo<T> G, const Phys<T> Ph, u
 // the call's register saves cost more than they free.)
 template <class T, int DIM, int MODE, bool SEAMLESS>
 __device__ __noinline__ void particle_tile(const Geo<T> G, const Phys<T> Ph, const TileCfg C, int c0x, int c0y,
-                                           int c0z, const V4<T> pa, const V4<T> pc, bool xsplit, uint32_t a,
-                                           const uint16_t *lstart,
+                                           int c0z, const V4<T> pa, const V4<T> pc, uint32_t a, const uint16_t *lstart,
                                            const V4<T> *spos, const V4<T> *__restrict__ vel, T mass,
                                            T *__restrict__ out_rho, T *pr_out, V4<T> *__restrict__ out_acc)
 {
@@ -325,8 +310,7 @@ __device__ __noinline__ void particle_tile(const Geo<T> G, const Phys<T> Ph, con
     PairAcc<T, MODE> A;
     acc_init(A, Ph, pa, vel, static_cast<const T *>(nullptr), a);
     const int c0[3] = {c0x, c0y, c0z};
-    walk_tile<T, DIM, MODE, false, SEAMLESS>(A, G, Ph, C, c0, pa, pc, xsplit, lstart, spos, nullptr, nullptr, nullptr,
-                                             nullptr);
+    walk_tile<T, DIM, MODE, false, SEAMLESS>(A, G, Ph, C, c0, pa, pc, lstart, spos, nullptr, nullptr, nullptr, nullptr);
     acc_store(A, Ph, a, mass, vel, out_rho, pr_out, out_acc, nullptr, nullptr);
 }
 
@@ -420,7 +404,7 @@ k_pair_tile(Geo<T> G, Phys<T> Ph, TileCfg C, const V4<T> *__restrict__ pos, cons
     // coordinates, the correctly rounded periodic displacement, and the walks
     // take the plain path. Tiles that do not meet this (lo != 0, a halo over
     // both seams) keep the per-pair seam path.
-    bool seamless = true, shifted = false, xsplit = false;
+    bool seamless = true, shifted = false;
     int lowk[3] = {0, 0, 0}, highk[3] = {0, 0, 0};
     T orig[3] = {T(0), T(0), T(0)};  // what the owned particles' staged coordinates lack
     {
@@ -441,7 +425,6 @@ k_pair_tile(Geo<T> G, Phys<T> Ph, TileCfg C, const V4<T> *__restrict__ pos, cons
                 shifted = true;
 #pragma unroll
                 for (int k = 0; k < DIM; ++k) orig[k] = highk[k] ? G.L[k] : T(0);
-                xsplit = lowk[0] || highk[0];
             } else {
                 seamless = false;
             }
@@ -610,9 +593,9 @@ k_pair_tile(Geo<T> G, Phys<T> Ph, TileCfg C, const V4<T> *__restrict__ pos, cons
                 // density pass: record the neighbours in walk order
                 NbRec rec{nbl.idx + lbase, (uint32_t)oc, nbl.cap / 4, 0};
                 if (seamless)
-                    walk_tile<T, DIM, MODE, true, true>(A, G, Ph, C, c0, pa, pc, xsplit, lstart, spos, svel, srho, sid, &rec);
+                    walk_tile<T, DIM, MODE, true, true>(A, G, Ph, C, c0, pa, pc, lstart, spos, svel, srho, sid, &rec);
                 else
-                    walk_tile<T, DIM, MODE, true, false>(A, G, Ph, C, c0, pa, pc, xsplit, lstart, spos, svel, srho, sid, &rec);
+                    walk_tile<T, DIM, MODE, true, false>(A, G, Ph, C, c0, pa, pc, lstart, spos, svel, srho, sid, &rec);
                 nbl.cnt[(size_t)blockIdx.x * oc + p] = rec.n <= nbl.cap ? (uint16_t)rec.n : kNbNone;
             } else if (MODE == 2 && listed && nbl.cnt[(size_t)blockIdx.x * oc + p] != kNbNone) {
                 // force pass: the density pass's list of this binning, same order
@@ -627,17 +610,17 @@ k_pair_tile(Geo<T> G, Phys<T> Ph, TileCfg C, const V4<T> *__restrict__ pos, cons
                 // a particle the density pass does not list (rare): out of line
                 if constexpr (MODE == 0) {
                     if (seamless)
-                        particle_tile<T, DIM, MODE, true>(G, Ph, C, c0[0], c0[1], c0[2], pa, pc, xsplit, a, lstart, spos, vel,
+                        particle_tile<T, DIM, MODE, true>(G, Ph, C, c0[0], c0[1], c0[2], pa, pc, a, lstart, spos, vel,
                                                           mass, out_rho, pr_out, out_acc);
                     else
-                        particle_tile<T, DIM, MODE, false>(G, Ph, C, c0[0], c0[1], c0[2], pa, pc, xsplit, a, lstart, spos, vel,
+                        particle_tile<T, DIM, MODE, false>(G, Ph, C, c0[0], c0[1], c0[2], pa, pc, a, lstart, spos, vel,
                                                            mass, out_rho, pr_out, out_acc);
                 }
                 continue;
             } else if (seamless) {
-                walk_tile<T, DIM, MODE, false, true>(A, G, Ph, C, c0, pa, pc, xsplit, lstart, spos, svel, srho, sid, nullptr);
+                walk_tile<T, DIM, MODE, false, true>(A, G, Ph, C, c0, pa, pc, lstart, spos, svel, srho, sid, nullptr);
             } else {
-                walk_tile<T, DIM, MODE, false, false>(A, G, Ph, C, c0, pa, pc, xsplit, lstart, spos, svel, srho, sid, nullptr);
+                walk_tile<T, DIM, MODE, false, false>(A, G, Ph, C, c0, pa, pc, lstart, spos, svel, srho, sid, nullptr);
             }
         }
         acc_store(A, Ph, a, mass, vel, out_rho, pr_out, out_acc, cnt, fpr);
