@@ -447,7 +447,8 @@ k_pair_tile(Geo<T> G, Phys<T> Ph, TileCfg C, const V4<T> *__restrict__ pos, cons
     // a tile whose halo lies inside the grid on every axis (no wrap, no
     // cell outside): each halo row of cells is one contiguous range of the
     // sorted particles, so the rows are counted and copied whole (not for
-    // the full force, whose walk then spills a register)
+    // the full force, whose walk then spills a register; and only where the
+    // particle area can hold the halo cells' 32-bit starts meanwhile)
     bool interior = MODE != 3 && C.nhalo * 4 <= C.cap * (int)sizeof(V4<T>);
 #pragma unroll
     for (int k = 0; k < 3; ++k)
